@@ -1,0 +1,204 @@
+"""CPU oracle for tetrahedral-mesh solid voxelization (test infrastructure).
+
+Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path (the CUDA library and
+its Python binding) never calls it and shares no code with it.
+
+Two independent oracles live here:
+
+* ``voxtet_oracle.c`` -- plain C, exact 128-bit integer determinants, the
+  paper's Theorem 1 sign patterns (Section 4) applied to every voxel-centre
+  sample in every tetrahedron's bounding box (Section 3, "Voxelization").
+  Loaded through ctypes after ``build()`` compiles it with gcc.
+* ``bigint_check`` -- pure Python integers, a different formulation
+  (orientation-normalised barycentric signs), for tiny inputs.
+
+Status codes: 0 ok, -1 bad argument, -2 resolution not a power of two in
+[1, 2^19], -3 vertex index out of range, -4 snapped coordinate beyond 2^21,
+-5 non-finite vertex coordinate.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from typing import Optional, Tuple
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "voxtet_oracle.c")
+_LIB_PATH = os.path.join(_HERE, "libvoxtet_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+OK, ERR_ARG, ERR_RES, ERR_INDEX, ERR_RANGE, ERR_NAN = 0, -1, -2, -3, -4, -5
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (OpenMP, no FP contraction)."""
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True, cwd=_HERE)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            lib = ctypes.CDLL(_LIB_PATH)
+            P = ctypes.c_void_p
+            i64, i32, f32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+            lib.voxtet_oracle_snap.argtypes = [P, i64, P, f32, i32, P]
+            lib.voxtet_oracle_snap.restype = ctypes.c_int
+            lib.voxtet_oracle_voxelize_fixed.argtypes = [P, i64, P, i64, i32, i32, i32, P, P]
+            lib.voxtet_oracle_voxelize_fixed.restype = ctypes.c_int
+            lib.voxtet_oracle_voxelize_fixed_slab.argtypes = [P, i64, P, i64, i32, i32, i32, i32, i32, P, P]
+            lib.voxtet_oracle_voxelize_fixed_slab.restype = ctypes.c_int
+            lib.voxtet_oracle_voxelize.argtypes = [P, i64, P, i64, P, f32, i32, i32, i32, P, P]
+            lib.voxtet_oracle_voxelize.restype = ctypes.c_int
+            lib.voxtet_oracle_all_pairs.argtypes = [P, i64, P, i64, i32, i32, P]
+            lib.voxtet_oracle_all_pairs.restype = ctypes.c_int
+            lib.voxtet_oracle_theorem1_dets.argtypes = [P, P, P, P, P, P]
+            lib.voxtet_oracle_theorem1_dets.restype = None
+            lib.voxtet_oracle_num_threads.argtypes = []
+            lib.voxtet_oracle_num_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> ctypes.c_void_p:
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def grid_words(res: int) -> int:
+    return res * res * ((res + 31) // 32)
+
+
+class OracleError(RuntimeError):
+    def __init__(self, status: int):
+        super().__init__(f"oracle status {status}")
+        self.status = status
+
+
+def snap(verts: np.ndarray, origin, voxel_size: float, res: int) -> Tuple[int, np.ndarray]:
+    lib = _load()
+    v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+    o = np.ascontiguousarray(np.asarray(origin, dtype=np.float32).reshape(3))
+    out = np.zeros((len(v), 3), dtype=np.int32)
+    st = lib.voxtet_oracle_snap(_ptr(v), len(v), _ptr(o), float(voxel_size), int(res), _ptr(out))
+    return st, out
+
+
+def voxelize_fixed(xyz: np.ndarray, tets: np.ndarray, res: int, mode: int = 0, n_threads: int = 0,
+                   with_stats: bool = False, raise_on_error: bool = True):
+    """Grid (uint32 [res, res, W]) of the union of closed tets on lattice coordinates."""
+    lib = _load()
+    x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    W = (res + 31) // 32 if res > 0 else 1
+    out = np.zeros(max(res, 1) * max(res, 1) * W, dtype=np.uint32)
+    stats = np.zeros(3, dtype=np.int64)
+    st = lib.voxtet_oracle_voxelize_fixed(_ptr(x), len(x), _ptr(t), len(t), int(res), int(mode),
+                                          int(n_threads), _ptr(out), _ptr(stats))
+    if st != OK:
+        if raise_on_error:
+            raise OracleError(st)
+        return (st, None, None) if with_stats else (st, None)
+    grid = out.reshape(res, res, W)
+    if with_stats:
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+    return grid
+
+
+def voxelize_fixed_slab(xyz: np.ndarray, tets: np.ndarray, res: int, z0: int, z1: int, mode: int = 0,
+                        n_threads: int = 0, with_stats: bool = False):
+    """Slices z0 <= l < z1 of the grid (uint32 [z1 - z0, res, W]); same semantics as ``voxelize_fixed``."""
+    lib = _load()
+    x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    W = (res + 31) // 32
+    out = np.zeros(max(z1 - z0, 1) * res * W, dtype=np.uint32)
+    stats = np.zeros(3, dtype=np.int64)
+    st = lib.voxtet_oracle_voxelize_fixed_slab(_ptr(x), len(x), _ptr(t), len(t), int(res), int(mode),
+                                               int(n_threads), int(z0), int(z1), _ptr(out), _ptr(stats))
+    if st != OK:
+        raise OracleError(st)
+    grid = out[: (z1 - z0) * res * W].reshape(z1 - z0, res, W)
+    if with_stats:
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+    return grid
+
+
+def voxelize(verts: np.ndarray, tets: np.ndarray, origin, voxel_size: float, res: int, mode: int = 0,
+             n_threads: int = 0, with_stats: bool = False, raise_on_error: bool = True):
+    """Grid of float32 vertices snapped to the 2^20 lattice, then voxelized."""
+    lib = _load()
+    v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    o = np.ascontiguousarray(np.asarray(origin, dtype=np.float32).reshape(3))
+    W = (res + 31) // 32 if res > 0 else 1
+    out = np.zeros(max(res, 1) * max(res, 1) * W, dtype=np.uint32)
+    stats = np.zeros(3, dtype=np.int64)
+    st = lib.voxtet_oracle_voxelize(_ptr(v), len(v), _ptr(t), len(t), _ptr(o), float(voxel_size), int(res),
+                                    int(mode), int(n_threads), _ptr(out), _ptr(stats))
+    if st != OK:
+        if raise_on_error:
+            raise OracleError(st)
+        return (st, None, None) if with_stats else (st, None)
+    grid = out.reshape(res, res, W)
+    if with_stats:
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+    return grid
+
+
+def all_pairs(xyz: np.ndarray, tets: np.ndarray, res: int, mode: int = 0) -> np.ndarray:
+    lib = _load()
+    x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    W = (res + 31) // 32
+    out = np.zeros(res * res * W, dtype=np.uint32)
+    st = lib.voxtet_oracle_all_pairs(_ptr(x), len(x), _ptr(t), len(t), int(res), int(mode), _ptr(out))
+    if st != OK:
+        raise OracleError(st)
+    return out.reshape(res, res, W)
+
+
+def theorem1_dets(A, B, C, D, P) -> Tuple[int, int, int, int]:
+    """(D_a, D_b, D_c, D_d) of Theorem 1 as Python ints, from the C oracle."""
+    lib = _load()
+    arrs = [np.ascontiguousarray(np.asarray(x, dtype=np.int64).reshape(3)) for x in (A, B, C, D, P)]
+    out = np.zeros(8, dtype=np.int64)
+    lib.voxtet_oracle_theorem1_dets(*[_ptr(a) for a in arrs], _ptr(out))
+    vals = []
+    for m in range(4):
+        hi, lo = int(out[2 * m]), int(out[2 * m + 1]) & ((1 << 64) - 1)
+        vals.append((hi << 64) | lo)
+    return tuple(vals)
+
+
+def num_threads() -> int:
+    return int(_load().voxtet_oracle_num_threads())
+
+
+def unpack(grid: np.ndarray, res: int) -> np.ndarray:
+    """Bit grid (uint32 [res, res, W]) -> bool array indexed [l, j, i] (z, y, x)."""
+    g = np.ascontiguousarray(grid, dtype=np.uint32).reshape(res, res, -1)
+    bits = np.unpackbits(g.view(np.uint8), axis=-1, bitorder="little")
+    return bits[..., :res].astype(bool)
+
+
+def pack(occ: np.ndarray) -> np.ndarray:
+    """Inverse of ``unpack``: bool [res, res, res] (z, y, x) -> uint32 [res, res, W]."""
+    res = occ.shape[0]
+    W = (res + 31) // 32
+    pad = np.zeros((res, res, W * 32), dtype=np.uint8)
+    pad[..., :res] = occ
+    return np.packbits(pad, axis=-1, bitorder="little").view(np.uint32).reshape(res, res, W)
