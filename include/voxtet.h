@@ -1,0 +1,140 @@
+/*
+ * voxtet.h -- C ABI of the GB300 (sm_103a) solid voxelizer for tetrahedral meshes.
+ *
+ * The operation is the voxelization step of arXiv 2106.01326 (Section 3,
+ * "Voxelization"): every voxel-centre sample that lies in some tetrahedron of
+ * the mesh is marked in a dense binary grid, using the point-in-tetrahedron
+ * test of Section 4, Theorem 1.  This library computes that grid exactly:
+ *
+ *   - Vertices are snapped to a fixed-point lattice on which the grid spans
+ *     [0, 2^20] per axis: X = round_half_even(((double)v - origin) / voxel_size
+ *     * 2^(20-k)) for res = 2^k, each double operation rounded to nearest.
+ *     |X| <= 2^21 is required (vertices may lie up to one grid extent outside).
+ *   - Voxel (i, j, l) is sampled at its centre ((2i+1)s, (2j+1)s, (2l+1)s),
+ *     s = 2^(19-k) lattice units.
+ *   - A sample is set iff it lies in the CLOSED tetrahedron (mode 0; Theorem 1
+ *     with non-strict comparisons) or its interior (mode 1; Theorem 1 as
+ *     stated) of at least one tetrahedron with non-zero signed volume
+ *     (Lemma 1.1's det(AB, AC, AD)).  Tetrahedra of either orientation are
+ *     accepted; zero-volume ones mark nothing.  The grid is a union, so it does
+ *     not depend on tetrahedron order, duplicates or overlaps.
+ *   - Every decision is exact: a single-precision filter with a proven error
+ *     bound answers the easy cases and exact 64/128-bit integer arithmetic the
+ *     rest, so results are bit-identical to an exact reference.
+ *
+ * Grid layout (out_bits): uint32 words, W = ceil(res / 32) words per x-row;
+ * bit (i, j, l) is word (l * res + j) * W + (i >> 5), bit (i & 31) (least
+ * significant bit = lowest x).  z is slowest, x fastest.  Padding bits of the
+ * last word of a row are zero whenever a call returns VOXTET_OK.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* / documented as DEVICE are CUDA device pointers; the
+ *     caller owns and allocates every buffer (mesh, grid, workspace).  The
+ *     library allocates no device memory.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; with opts->sync = 1 the call synchronizes it and
+ *     returns device-detected errors, otherwise they are read later with
+ *     voxtet_last_status().
+ *   - Arguments are validated on the host before anything is launched; a
+ *     rejected call returns a negative status and touches nothing.
+ *   - Calls on different streams with disjoint workspaces and grids are
+ *     independent.  Two in-flight calls sharing a workspace race.
+ */
+#ifndef VOXTET_H
+#define VOXTET_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VOXTET_OK = 0,
+    VOXTET_ERR_ARG = -1,       /* null pointer, negative size, bad option, non-positive voxel_size */
+    VOXTET_ERR_RES = -2,       /* res not a power of two in [1, VOXTET_MAX_RES] */
+    VOXTET_ERR_INDEX = -3,     /* a tetrahedron names a vertex outside [0, n_verts) (device-detected) */
+    VOXTET_ERR_RANGE = -4,     /* a snapped coordinate exceeds 2^21 in magnitude (device-detected) */
+    VOXTET_ERR_NAN = -5,       /* a vertex coordinate is NaN or infinite (device-detected) */
+    VOXTET_ERR_WORKSPACE = -6, /* workspace missing, misaligned or smaller than voxtet_workspace_size() */
+    VOXTET_ERR_CUDA = -7,      /* a CUDA runtime call or launch failed */
+    VOXTET_ERR_TIMEOUT = -8,   /* a bounded device-side wait gave up (batched/served paths) */
+    VOXTET_ERR_NOMEM = -9      /* a caller-provided arena is too small for the requested jobs */
+} voxtet_status;
+
+/* Largest grid resolution accepted by the GPU entry points (a 16384^3 grid of
+ * bits is 512 GiB, beyond any single device). */
+#define VOXTET_MAX_RES 8192
+
+typedef struct {
+    int32_t mode;       /* 0 = closed tetrahedra (default), 1 = open interiors (Theorem 1 as stated) */
+    int32_t accumulate; /* 0 = clear out_bits first (default), 1 = OR into its current contents */
+    int32_t use_filter; /* 1 = single-precision filter + exact fallback (default), 0 = exact integer only */
+    int32_t sync;       /* 1 = synchronize the stream and return device-detected status (default 1) */
+    int32_t span_rows;  /* x-rows per work item of the scanline kernel; 0 = automatic */
+    int32_t block;      /* threads per block of the scanline kernel; 0 = automatic (only 256 is accepted) */
+    int32_t profile;    /* 1 = record CUDA events around the main kernel on `stream` (see voxtet_stats) */
+    int32_t reserved;
+} voxtet_opts;
+
+/* Counters the last call on a workspace left in it (read with voxtet_read_stats). */
+typedef struct {
+    uint64_t spans;           /* work items (tet, run of x-rows) distributed to threads */
+    uint64_t rows;            /* x-rows of tet bounding boxes visited */
+    uint64_t fallback_rows;   /* rows whose interval the filter could not certify (solved exactly) */
+    uint64_t degenerate_tets; /* tetrahedra with zero signed volume (skipped) */
+    uint64_t wide_tets;       /* tetrahedra wider than 2^20 lattice units (128-bit exact path) */
+    uint64_t kernel_ns;       /* device time of the main kernel of the last profiled call on this thread, else 0 */
+    uint64_t reserved[2];
+} voxtet_stats;
+
+/* Fill *opts with the defaults listed above. */
+void voxtet_default_opts(voxtet_opts *opts);
+
+/* Bytes of device workspace a call with these sizes needs (>= 256; the
+ * workspace must be 256-byte aligned).  It holds a 256-byte status/counter
+ * header and the snapped vertices (16 B per vertex).  Returns 0 for negative
+ * sizes. */
+size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res);
+
+/* Voxelize a mesh given in world coordinates (Section 3, "Voxelization";
+ * point test of Section 4, Theorem 1).
+ *   d_verts      DEVICE float32 [n_verts][3] (x, y, z), any alignment of 4 bytes
+ *   d_tets       DEVICE int32 [n_tets][4] vertex indices, 16-byte aligned
+ *   grid_origin  HOST float[3]: world position of the grid's lower corner
+ *   voxel_size   HOST: edge length of a (cubic) voxel, > 0 and finite
+ *   res          voxels per axis: a power of two in [1, VOXTET_MAX_RES]
+ *   d_out_bits   DEVICE uint32 [res * res * W] (layout above), 4-byte aligned
+ *   d_workspace  DEVICE scratch of voxtet_workspace_size() bytes, 256-byte aligned
+ *   opts         HOST, may be NULL for defaults
+ * Returns VOXTET_OK or a negative voxtet_status.  n_tets = 0 yields an empty
+ * grid.  On a device-detected error the grid contents are unspecified. */
+int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                  const float grid_origin[3], float voxel_size, int32_t res, uint32_t *d_out_bits,
+                  void *d_workspace, size_t ws_bytes, const voxtet_opts *opts, void *stream);
+
+/* Same operation on vertices already on the 2^20-per-grid lattice
+ * (d_xyz: DEVICE int32 [n_verts][3], |X| <= 2^21), skipping the snap. */
+int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                        int32_t res, uint32_t *d_out_bits, void *d_workspace, size_t ws_bytes,
+                        const voxtet_opts *opts, void *stream);
+
+/* Synchronize `stream` and return the device-detected status the last call on
+ * this workspace recorded (VOXTET_OK if none). */
+int voxtet_last_status(const void *d_workspace, void *stream);
+
+/* Synchronize `stream` and copy the last call's counters to *out (HOST). */
+int voxtet_read_stats(const void *d_workspace, voxtet_stats *out, void *stream);
+
+/* Static English text for a status code. */
+const char *voxtet_strerror(int status);
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+uint64_t voxtet_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VOXTET_H */

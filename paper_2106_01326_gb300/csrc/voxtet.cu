@@ -1,0 +1,780 @@
+// voxtet.cu -- sm_103a kernels and C ABI of the tetrahedral-mesh solid voxelizer.
+//
+// The operation is Section 3 ("Voxelization") of arXiv 2106.01326: visit the
+// bounding box of every tetrahedron and mark the voxel-centre samples that pass
+// the point-in-tetrahedron test of Section 4, Theorem 1 (closed reading by
+// default).  The paper visits every sample of every box one by one; here the
+// four affine orientation values of a tet are solved along each x-row of its
+// box for the whole run of passing samples at once, so the per-sample test
+// becomes a per-row interval.
+//
+// Kernels (one stream, in order):
+//   k_prologue   zero the workspace header and (unless accumulating) the grid
+//   k_snap       float vertices -> lattice int4 (x, y, z, flag); k_load_fixed
+//                does the range check for vertices already on the lattice
+//   k_voxelize   persistent; each block repeatedly claims a tile of tets and
+//                (1) computes per tet the sample box, orientation and row count,
+//                    staging the exact and filter data in shared memory,
+//                (2) splits the tile into spans of at most R x-rows with a
+//                    block-wide exclusive prefix sum,
+//                (3) solves every row of every span for its sample interval
+//                    (filter + exact fallback), and
+//                (4) ORs the interval into the bit grid: whole 32-bit words are
+//                    stored, the two partial edge words use atomicOr since other
+//                    tets may share them.
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cmath>
+#include <cstring>
+
+#include "voxtet.h"
+#include "tet_math.cuh"
+
+namespace voxtet {
+
+constexpr int kBlock = 256;              // threads per block == tets per tile
+constexpr int kMaxSpansPerTet = 1 << 22; // keeps a tile's span count within 32 bits
+constexpr int kDefaultSpanRows = 16;
+
+// Workspace header (first 256 bytes of the workspace).
+struct Header {
+  int status_bits;
+  int pad0;
+  unsigned long long tile_counter;
+  unsigned long long spans;
+  unsigned long long rows;
+  unsigned long long fallback_rows;
+  unsigned long long degenerate;
+  unsigned long long wide;
+  unsigned long long reserved[25];
+};
+static_assert(sizeof(Header) == 256, "header is 256 bytes");
+
+// Per-tet record staged in shared memory for the span phase.
+struct __align__(16) TetRec {
+  float alpha[4], beta[4], gamma[4], delta[4];  // filter data, slot order
+  Exact<i64> X;                                 // exact data, slot order
+  int i0, j0, l0, na;
+  int nb, nc, meta, rows_per_span;  // meta: nup | nlo << 4 | wide << 8
+  long long tet;
+  long long pad;
+};
+
+struct Params {
+  const int4 *verts4;
+  const int4 *tets;
+  long long n_tets;
+  long long n_verts;
+  uint32_t *out;
+  Header *hdr;
+  int res;
+  int W;
+  int sh;          // 20 - log2(res)
+  int span_rows;
+};
+
+// ------------------------------------------------------------------ small kernels
+
+__global__ void k_prologue(Header *hdr, uint32_t *out, long long n_words, int clear) {
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (tid < 64) reinterpret_cast<uint32_t *>(hdr)[tid] = 0u;
+  if (!clear) return;
+  if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    uint4 *o4 = reinterpret_cast<uint4 *>(out);
+    const long long n4 = n_words >> 2;
+    for (long long i = tid; i < n4; i += stride) o4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (long long i = (n4 << 2) + tid; i < n_words; i += stride) out[i] = 0u;
+  } else {
+    for (long long i = tid; i < n_words; i += stride) out[i] = 0u;
+  }
+}
+
+// X = round_half_even(((double)v - o) / h * 2^(20-k)), each double operation rounded to
+// nearest.  When h is a power of two the quotient is exact and the host passes
+// mul = 2^(20-k) / h instead (identical result, no double division).
+__global__ void k_snap(const float *__restrict__ v, long long n, double ox, double oy, double oz, double h,
+                       double scale, double mul, int use_mul, int4 *__restrict__ out, Header *hdr) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int err = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int X[3];
+    int flag = 0;
+    const double o[3] = {ox, oy, oz};
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float f = v[3 * i + q];
+      X[q] = 0;
+      if (!isfinite(f)) {
+        flag = 1;
+        err |= kErrNan;
+        continue;
+      }
+      const double d = __dsub_rn((double)f, o[q]);
+      const double x = use_mul ? __dmul_rn(d, mul) : __dmul_rn(__ddiv_rn(d, h), scale);
+      const long long r = __double2ll_rn(x);
+      if (r < -kCoordLimit || r > kCoordLimit) {
+        flag = 1;
+        err |= kErrRange;
+        continue;
+      }
+      X[q] = (int)r;
+    }
+    out[i] = make_int4(X[0], X[1], X[2], flag);
+  }
+  if (err) atomicOr(&hdr->status_bits, err);
+}
+
+__global__ void k_load_fixed(const int *__restrict__ xyz, long long n, int4 *__restrict__ out, Header *hdr) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  int err = 0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+    const bool bad = x < -kCoordLimit || x > kCoordLimit || y < -kCoordLimit || y > kCoordLimit ||
+                     z < -kCoordLimit || z > kCoordLimit;
+    if (bad) err |= kErrRange;
+    out[i] = make_int4(bad ? 0 : x, bad ? 0 : y, bad ? 0 : z, bad ? 1 : 0);
+  }
+  if (err) atomicOr(&hdr->status_bits, err);
+}
+
+// ------------------------------------------------------------------ OR writes
+
+// OR the samples x0..x1 (inclusive, absolute x indices) into one row of words.
+__device__ __forceinline__ void or_span(uint32_t *__restrict__ row, int x0, int x1) {
+  const int w0 = x0 >> 5, w1 = x1 >> 5;
+  const uint32_t m0 = 0xFFFFFFFFu << (x0 & 31);
+  const uint32_t m1 = 0xFFFFFFFFu >> (31 - (x1 & 31));
+  if (w0 == w1) {
+    const uint32_t m = m0 & m1;
+    if (m == 0xFFFFFFFFu) row[w0] = m;
+    else atomicOr(row + w0, m);
+    return;
+  }
+  if (m0 == 0xFFFFFFFFu) row[w0] = m0;
+  else atomicOr(row + w0, m0);
+  for (int w = w0 + 1; w < w1; ++w) row[w] = 0xFFFFFFFFu;
+  if (m1 == 0xFFFFFFFFu) row[w1] = m1;
+  else atomicOr(row + w1, m1);
+}
+
+// ------------------------------------------------------------------ tet setup (phase 1)
+
+__device__ __forceinline__ void load_tet_vertices(const Params &p, const int4 q, int3 V[4], int &flags) {
+  const int4 A = p.verts4[q.x], B = p.verts4[q.y], C = p.verts4[q.z], D = p.verts4[q.w];
+  V[0] = make_int3(A.x, A.y, A.z);
+  V[1] = make_int3(B.x, B.y, B.z);
+  V[2] = make_int3(C.x, C.y, C.z);
+  V[3] = make_int3(D.x, D.y, D.z);
+  flags = A.w | B.w | C.w | D.w;
+}
+
+// Fills rec for tet t and returns its span count (0 if it marks nothing).
+template <bool FILTER>
+__device__ uint32_t setup_tet(const Params &p, long long t, TetRec &rec, int &err, unsigned &n_degenerate,
+                              unsigned &n_wide) {
+  const int4 q = p.tets[t];
+  const unsigned long long nv = (unsigned long long)p.n_verts;
+  if ((unsigned long long)(unsigned)q.x >= nv || (unsigned long long)(unsigned)q.y >= nv ||
+      (unsigned long long)(unsigned)q.z >= nv || (unsigned long long)(unsigned)q.w >= nv || q.x < 0 || q.y < 0 ||
+      q.z < 0 || q.w < 0) {
+    err |= kErrIndex;
+    return 0;
+  }
+  int3 V[4];
+  int flags;
+  load_tet_vertices(p, q, V, flags);
+  if (flags) return 0;  // a vertex failed the snap; its error is already recorded
+  Box bx;
+  const int E = tet_box(V, p.sh, p.res, bx);
+  const int sg = v6_sign(V, E);
+  if (sg == 0) {
+    ++n_degenerate;
+    return 0;
+  }
+  if (bx.na <= 0 || bx.nb <= 0 || bx.nc <= 0) return 0;
+  if (sg < 0) {
+    const int3 tmp = V[2];
+    V[2] = V[3];
+    V[3] = tmp;
+  }
+  const uint32_t rows = (uint32_t)bx.nb * (uint32_t)bx.nc;
+  uint32_t R = (uint32_t)p.span_rows;
+  const uint32_t need = (rows + kMaxSpansPerTet - 1) / kMaxSpansPerTet;
+  if (R < need) R = need;
+  rec.i0 = bx.i0;
+  rec.j0 = bx.j0;
+  rec.l0 = bx.l0;
+  rec.na = bx.na;
+  rec.nb = bx.nb;
+  rec.nc = bx.nc;
+  rec.rows_per_span = (int)R;
+  rec.tet = t;
+  if (E <= kNarrowExtent) {
+    Exact<i64> X;
+    exact_setup<i64>(V, bx, p.sh, X);
+    int slot[4], nup = 0, nlo = 0;
+    slot_order<i64>(X, slot, nup, nlo);
+    const float fb = (float)(bx.nb - 1), fc = (float)(bx.nc - 1);
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int q = slot[m];
+      rec.X.L[q] = X.L[m];
+      rec.X.Dx[q] = X.Dx[m];
+      rec.X.Dy[q] = X.Dy[m];
+      rec.X.Dz[q] = X.Dz[m];
+      if (FILTER && X.Dx[m] != 0) {
+        float a, b, g, d;
+        filter_slot(X.L[m], X.Dx[m], X.Dy[m], X.Dz[m], fb, fc, a, b, g, d);
+        rec.alpha[q] = a;
+        rec.beta[q] = b;
+        rec.gamma[q] = g;
+        rec.delta[q] = d;
+      }
+    }
+    rec.meta = nup | (nlo << 4);
+  } else {
+    rec.meta = 1 << 8;
+    ++n_wide;
+  }
+  return (rows + R - 1) / R;
+}
+
+// ------------------------------------------------------------------ span phase
+
+struct RowCounters {
+  unsigned rows = 0, fallback = 0;
+};
+
+// Tets wider than 2^20 lattice units: 128-bit exact arithmetic for every row.
+template <bool STRICT>
+__device__ __noinline__ void span_wide(const Params &p, const TetRec &rec, uint32_t r0, uint32_t r1,
+                                       RowCounters &ctr) {
+  const int4 q = p.tets[rec.tet];
+  int3 V[4];
+  int flags;
+  load_tet_vertices(p, q, V, flags);
+  Box bx;
+  const int E = tet_box(V, p.sh, p.res, bx);
+  if (v6_sign(V, E) < 0) {
+    const int3 tmp = V[2];
+    V[2] = V[3];
+    V[3] = tmp;
+  }
+  Exact<i128> X;
+  exact_setup<i128>(V, bx, p.sh, X);
+  int slot[4], nup = 0, nlo = 0;
+  slot_order<i128>(X, slot, nup, nlo);
+  permute_slots<i128>(X, slot);
+  const int nb = rec.nb;
+  for (uint32_t r = r0; r < r1; ++r) {
+    const int c = (int)(r / (uint32_t)nb), b = (int)(r - (uint32_t)c * nb);
+    int lo, hi;
+    ++ctr.rows;
+    if (exact_row<STRICT, i128>(X, nup, nlo, rec.na, b, c, lo, hi)) {
+      uint32_t *row = p.out + ((size_t)(rec.l0 + c) * p.res + (rec.j0 + b)) * p.W;
+      or_span(row, rec.i0 + lo, rec.i0 + hi);
+    }
+  }
+}
+
+template <bool STRICT, bool FILTER>
+__device__ __forceinline__ void span_rows(const Params &p, const TetRec &rec, uint32_t r0, uint32_t r1,
+                                          RowCounters &ctr) {
+  const int meta = rec.meta;
+  if (meta >> 8) {
+    span_wide<STRICT>(p, rec, r0, r1, ctr);
+    return;
+  }
+  const int nup = meta & 7, nlo = (meta >> 4) & 7, nf = nup + nlo;
+  const int na = rec.na, nb = rec.nb;
+  float be[4], de[4], ac[4];
+  i64 Lc[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    be[m] = rec.beta[m];
+    de[m] = rec.delta[m];
+  }
+  int c = (int)(r0 / (uint32_t)nb);
+  int b = (int)(r0 - (uint32_t)c * nb);
+  auto set_slice = [&](int cc) {
+    const float cf = (float)cc;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      if (FILTER) ac[m] = __fmaf_rn(rec.gamma[m], cf, rec.alpha[m]);
+      if (m >= nf) Lc[m] = rec.X.L[m] + rec.X.Dz[m] * (i64)cc;  // whole-row slots only
+    }
+  };
+  set_slice(c);
+  uint32_t *row = p.out + ((size_t)(rec.l0 + c) * p.res + (rec.j0 + b)) * p.W;
+  const float fhi0 = (float)(na - 1);
+  for (uint32_t r = r0; r < r1; ++r) {
+    int lo_i = 0, hi_i = -1;
+    bool ok;
+    if (FILTER) {
+      const float bf = (float)b;
+      float lo = 0.f, hi = fhi0;
+      bool amb = false;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (m < nf) {
+          const float t = __fmaf_rn(be[m], bf, ac[m]);
+          const float tl = __fsub_rd(t, de[m]);
+          const float th = __fadd_ru(t, de[m]);
+          float v;
+          if (STRICT) {
+            const float cc = ceilf(tl);
+            amb |= cc < th;
+            v = cc - 1.f;
+          } else {
+            const float f = floorf(th);
+            amb |= f > tl;
+            v = f;
+          }
+          if (m < nup) hi = fminf(hi, v);
+          else lo = fmaxf(lo, -v);
+        }
+      }
+      ok = lo <= hi;
+      if (nf < 4) {
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+          if (m >= nf) ok = ok && lam_ok<STRICT, i64>(Lc[m] + rec.X.Dy[m] * (i64)b);
+      }
+      if (amb) {
+        ++ctr.fallback;
+        ok = exact_row<STRICT, i64>(rec.X, nup, nlo, na, b, c, lo_i, hi_i);
+      } else if (ok) {
+        lo_i = (int)lo;
+        hi_i = (int)hi;
+      }
+    } else {
+      ok = exact_row<STRICT, i64>(rec.X, nup, nlo, na, b, c, lo_i, hi_i);
+    }
+    ++ctr.rows;
+    if (ok) or_span(row, rec.i0 + lo_i, rec.i0 + hi_i);
+    if (++b == nb) {
+      b = 0;
+      ++c;
+      if (r + 1 < r1) set_slice(c);
+      row = p.out + ((size_t)(rec.l0 + c) * p.res + rec.j0) * p.W;
+    } else {
+      row += p.W;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ the fused kernel
+
+template <bool STRICT, bool FILTER>
+__global__ void __launch_bounds__(kBlock, 2) k_voxelize(Params p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TetRec *recs = reinterpret_cast<TetRec *>(smem_raw);
+  __shared__ uint32_t off[kBlock + 1];
+  __shared__ uint32_t warp_tot[kBlock / 32];
+  __shared__ unsigned long long tile_s;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int err = 0;
+  unsigned n_degenerate = 0, n_wide = 0;
+  unsigned long long n_spans = 0;
+  RowCounters ctr;
+
+  for (;;) {
+    if (tid == 0) tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
+    __syncthreads();
+    const long long base = (long long)tile_s * kBlock;
+    if (base >= p.n_tets) break;
+
+    // (1) per-tet box, orientation, row count
+    const long long t = base + tid;
+    uint32_t cnt = 0;
+    if (t < p.n_tets) cnt = setup_tet<FILTER>(p, t, recs[tid], err, n_degenerate, n_wide);
+
+    // (2) block-wide exclusive prefix sum of span counts
+    uint32_t x = cnt;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_tot[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      uint32_t w = lane < kBlock / 32 ? warp_tot[lane] : 0u;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+        if (lane >= d) w += y;
+      }
+      if (lane < kBlock / 32) warp_tot[lane] = w;  // inclusive warp prefix
+    }
+    __syncthreads();
+    const uint32_t warp_base = warp ? warp_tot[warp - 1] : 0u;
+    off[tid] = warp_base + x - cnt;
+    if (tid == kBlock - 1) off[kBlock] = warp_base + x;
+    __syncthreads();
+    const uint32_t total = off[kBlock];
+    n_spans += tid == 0 ? total : 0;
+
+    // (3)+(4) spans: largest slot u with off[u] <= s owns span s
+    for (uint32_t s = tid; s < total; s += kBlock) {
+      int a = 0, bnd = kBlock - 1;
+      while (a < bnd) {
+        const int mid = (a + bnd + 1) >> 1;
+        if (off[mid] <= s) a = mid;
+        else bnd = mid - 1;
+      }
+      const TetRec &rec = recs[a];
+      const uint32_t R = (uint32_t)rec.rows_per_span;
+      const uint32_t rows = (uint32_t)rec.nb * (uint32_t)rec.nc;
+      const uint32_t r0 = (s - off[a]) * R;
+      const uint32_t r1 = min(r0 + R, rows);
+      span_rows<STRICT, FILTER>(p, rec, r0, r1, ctr);
+    }
+    __syncthreads();
+  }
+
+  // counters: one atomic per warp
+  unsigned long long rows_w = ctr.rows, fb_w = ctr.fallback, deg_w = n_degenerate, wide_w = n_wide;
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    rows_w += __shfl_down_sync(0xFFFFFFFFu, rows_w, d);
+    fb_w += __shfl_down_sync(0xFFFFFFFFu, fb_w, d);
+    deg_w += __shfl_down_sync(0xFFFFFFFFu, deg_w, d);
+    wide_w += __shfl_down_sync(0xFFFFFFFFu, wide_w, d);
+  }
+  err = __reduce_or_sync(0xFFFFFFFFu, err);
+  if (lane == 0) {
+    if (rows_w) atomicAdd(&p.hdr->rows, rows_w);
+    if (fb_w) atomicAdd(&p.hdr->fallback_rows, fb_w);
+    if (deg_w) atomicAdd(&p.hdr->degenerate, deg_w);
+    if (wide_w) atomicAdd(&p.hdr->wide, wide_w);
+    if (err) atomicOr(&p.hdr->status_bits, err);
+  }
+  if (tid == 0 && n_spans) atomicAdd(&p.hdr->spans, n_spans);
+}
+
+// ------------------------------------------------------------------ host side
+
+static std::atomic<unsigned long long> g_launches{0};
+
+constexpr int kMaxDevices = 64;
+struct DeviceInfo {
+  int sms = 0;
+  int occ[4] = {0, 0, 0, 0};  // blocks per SM of k_voxelize<STRICT, FILTER>
+  bool ready = false;
+};
+static DeviceInfo g_dev[kMaxDevices];
+static std::atomic<int> g_dev_lock{0};
+
+// Events of the last profiled call, per host thread (the elapsed time is read back
+// by voxtet_read_stats on the same thread).
+struct ProfileEvents {
+  cudaEvent_t start = nullptr, stop = nullptr;
+  int device = -1;
+  bool pending = false;
+};
+static thread_local ProfileEvents t_prof;
+
+static cudaError_t profile_begin(cudaStream_t stream) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (t_prof.device != dev || !t_prof.start) {
+    if (t_prof.start) {
+      cudaEventDestroy(t_prof.start);
+      cudaEventDestroy(t_prof.stop);
+    }
+    e = cudaEventCreate(&t_prof.start);
+    if (e == cudaSuccess) e = cudaEventCreate(&t_prof.stop);
+    if (e != cudaSuccess) return e;
+    t_prof.device = dev;
+  }
+  t_prof.pending = false;
+  return cudaEventRecord(t_prof.start, stream);
+}
+
+static size_t rec_smem() { return (size_t)kBlock * sizeof(TetRec); }
+
+template <bool S, bool F>
+static cudaError_t prepare_kernel(int &occ) {
+  cudaError_t e = cudaFuncSetAttribute(k_voxelize<S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)rec_smem());
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize<S, F>, kBlock, rec_smem());
+}
+
+static cudaError_t device_info(DeviceInfo *&out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  DeviceInfo &d = g_dev[dev];
+  if (!d.ready) {
+    while (g_dev_lock.exchange(1)) {
+    }
+    if (!d.ready) {
+      e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+      if (e == cudaSuccess) e = prepare_kernel<false, false>(d.occ[0]);
+      if (e == cudaSuccess) e = prepare_kernel<false, true>(d.occ[1]);
+      if (e == cudaSuccess) e = prepare_kernel<true, false>(d.occ[2]);
+      if (e == cudaSuccess) e = prepare_kernel<true, true>(d.occ[3]);
+      if (e == cudaSuccess) d.ready = true;
+    }
+    g_dev_lock.store(0);
+    if (e != cudaSuccess) return e;
+  }
+  out = &d;
+  return cudaSuccess;
+}
+
+static int log2_res(int res) {
+  if (res < 1 || res > VOXTET_MAX_RES || (res & (res - 1))) return -1;
+  int k = 0;
+  while ((1 << k) != res) ++k;
+  return k;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+static int map_status_bits(int bits) {
+  if (bits & kErrNan) return VOXTET_ERR_NAN;
+  if (bits & kErrRange) return VOXTET_ERR_RANGE;
+  if (bits & kErrIndex) return VOXTET_ERR_INDEX;
+  return VOXTET_OK;
+}
+
+static void resolve_opts(const voxtet_opts *in, voxtet_opts &o) {
+  voxtet_default_opts(&o);
+  if (in) o = *in;
+}
+
+static int check_opts(const voxtet_opts &o) {
+  if (o.mode != 0 && o.mode != 1) return VOXTET_ERR_ARG;
+  if (o.accumulate != 0 && o.accumulate != 1) return VOXTET_ERR_ARG;
+  if (o.use_filter != 0 && o.use_filter != 1) return VOXTET_ERR_ARG;
+  if (o.sync != 0 && o.sync != 1) return VOXTET_ERR_ARG;
+  if (o.span_rows < 0 || o.span_rows > (1 << 20)) return VOXTET_ERR_ARG;
+  if (o.block != 0 && o.block != kBlock) return VOXTET_ERR_ARG;
+  if (o.profile != 0 && o.profile != 1) return VOXTET_ERR_ARG;
+  return VOXTET_OK;
+}
+
+// Shared tail of both entry points: vertices are already in the workspace.
+static int run_voxelize(const int4 *verts4, long long n_verts, const int32_t *tets, long long n_tets, int res,
+                        int k, uint32_t *out, Header *hdr, const voxtet_opts &o, cudaStream_t stream) {
+  DeviceInfo *dev = nullptr;
+  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+  if (n_tets > 0) {
+    Params p;
+    p.verts4 = verts4;
+    p.tets = reinterpret_cast<const int4 *>(tets);
+    p.n_tets = n_tets;
+    p.n_verts = n_verts;
+    p.out = out;
+    p.hdr = hdr;
+    p.res = res;
+    p.W = (res + 31) / 32;
+    p.sh = kLatticeBits - k;
+    p.span_rows = o.span_rows > 0 ? o.span_rows : kDefaultSpanRows;
+    const long long tiles = (n_tets + kBlock - 1) / kBlock;
+    const int variant = (o.mode == 1 ? 2 : 0) + (o.use_filter ? 1 : 0);
+    long long grid = (long long)dev->sms * (dev->occ[variant] > 0 ? dev->occ[variant] : 1);
+    if (grid > tiles) grid = tiles;
+    const size_t sm = rec_smem();
+    if (o.profile && profile_begin(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+    switch (variant) {
+      case 0: k_voxelize<false, false><<<(unsigned)grid, kBlock, sm, stream>>>(p); break;
+      case 1: k_voxelize<false, true><<<(unsigned)grid, kBlock, sm, stream>>>(p); break;
+      case 2: k_voxelize<true, false><<<(unsigned)grid, kBlock, sm, stream>>>(p); break;
+      default: k_voxelize<true, true><<<(unsigned)grid, kBlock, sm, stream>>>(p); break;
+    }
+    g_launches.fetch_add(1);
+    if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
+    if (o.profile) {
+      if (cudaEventRecord(t_prof.stop, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+      t_prof.pending = true;
+    }
+  }
+  if (o.sync) {
+    if (cudaStreamSynchronize(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+    int bits = 0;
+    if (cudaMemcpy(&bits, &hdr->status_bits, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return VOXTET_ERR_CUDA;
+    return map_status_bits(bits);
+  }
+  return VOXTET_OK;
+}
+
+static int launch_prologue(Header *hdr, uint32_t *out, long long n_words, int clear, cudaStream_t stream) {
+  DeviceInfo *dev = nullptr;
+  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+  long long blocks = clear ? (n_words / 4 + 255) / 256 : 1;
+  const long long cap = (long long)dev->sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_prologue<<<(unsigned)blocks, 256, 0, stream>>>(hdr, out, n_words, clear);
+  g_launches.fetch_add(1);
+  return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
+}
+
+static int grid_blocks(long long n, int per_block, int sms) {
+  long long b = (n + per_block - 1) / per_block;
+  const long long cap = (long long)sms * 16;
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+static int common_checks(long long n_verts, const void *tets, long long n_tets, int res, const uint32_t *out,
+                         void *ws, size_t ws_bytes, const voxtet_opts &o, int &k) {
+  int st = check_opts(o);
+  if (st != VOXTET_OK) return st;
+  k = log2_res(res);
+  if (k < 0) return VOXTET_ERR_RES;
+  if (n_verts < 0 || n_tets < 0 || n_verts > 0x7FFFFFFFLL) return VOXTET_ERR_ARG;
+  if (!out) return VOXTET_ERR_ARG;
+  if (n_tets > 0 && (!tets || (reinterpret_cast<uintptr_t>(tets) & 15))) return VOXTET_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(out) & 3) return VOXTET_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return VOXTET_ERR_WORKSPACE;
+  if (ws_bytes < voxtet_workspace_size(n_tets, n_verts, res)) return VOXTET_ERR_WORKSPACE;
+  return VOXTET_OK;
+}
+
+}  // namespace voxtet
+
+using namespace voxtet;
+
+extern "C" {
+
+void voxtet_default_opts(voxtet_opts *o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->mode = 0;
+  o->accumulate = 0;
+  o->use_filter = 1;
+  o->sync = 1;
+  o->span_rows = 0;
+  o->block = 0;
+  o->profile = 0;
+}
+
+size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res) {
+  (void)res;
+  if (n_tets < 0 || n_verts < 0) return 0;
+  return sizeof(Header) + align256((size_t)n_verts * sizeof(int4));
+}
+
+int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                  const float grid_origin[3], float voxel_size, int32_t res, uint32_t *d_out_bits, void *d_workspace,
+                  size_t ws_bytes, const voxtet_opts *opts, void *stream_) {
+  voxtet_opts o;
+  resolve_opts(opts, o);
+  int k = 0;
+  int st = common_checks(n_verts, d_tets, n_tets, res, d_out_bits, d_workspace, ws_bytes, o, k);
+  if (st != VOXTET_OK) return st;
+  if (!grid_origin) return VOXTET_ERR_ARG;
+  if (n_verts > 0 && (!d_verts || (reinterpret_cast<uintptr_t>(d_verts) & 3))) return VOXTET_ERR_ARG;
+  if (!(voxel_size > 0.0f) || !std::isfinite(voxel_size)) return VOXTET_ERR_ARG;
+  for (int q = 0; q < 3; ++q)
+    if (!std::isfinite(grid_origin[q])) return VOXTET_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  Header *hdr = reinterpret_cast<Header *>(d_workspace);
+  int4 *verts4 = reinterpret_cast<int4 *>(reinterpret_cast<char *>(d_workspace) + sizeof(Header));
+  const long long W = (res + 31) / 32;
+  st = launch_prologue(hdr, d_out_bits, (long long)res * res * W, o.accumulate ? 0 : 1, stream);
+  if (st != VOXTET_OK) return st;
+  DeviceInfo *dev = nullptr;
+  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+  if (n_verts > 0) {
+    const double h = (double)voxel_size;
+    const double scale = std::ldexp(1.0, kLatticeBits - k);
+    int e2 = 0;
+    const double mant = std::frexp(h, &e2);
+    const int use_mul = mant == 0.5 ? 1 : 0;
+    const double mul = use_mul ? std::ldexp(1.0, kLatticeBits - k - (e2 - 1)) : 0.0;
+    k_snap<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(
+        d_verts, n_verts, (double)grid_origin[0], (double)grid_origin[1], (double)grid_origin[2], h, scale, mul,
+        use_mul, verts4, hdr);
+    g_launches.fetch_add(1);
+    if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
+  }
+  return run_voxelize(verts4, n_verts, d_tets, n_tets, res, k, d_out_bits, hdr, o, stream);
+}
+
+int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_tets, int64_t n_tets, int32_t res,
+                        uint32_t *d_out_bits, void *d_workspace, size_t ws_bytes, const voxtet_opts *opts,
+                        void *stream_) {
+  voxtet_opts o;
+  resolve_opts(opts, o);
+  int k = 0;
+  int st = common_checks(n_verts, d_tets, n_tets, res, d_out_bits, d_workspace, ws_bytes, o, k);
+  if (st != VOXTET_OK) return st;
+  if (n_verts > 0 && (!d_xyz || (reinterpret_cast<uintptr_t>(d_xyz) & 3))) return VOXTET_ERR_ARG;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  Header *hdr = reinterpret_cast<Header *>(d_workspace);
+  int4 *verts4 = reinterpret_cast<int4 *>(reinterpret_cast<char *>(d_workspace) + sizeof(Header));
+  const long long W = (res + 31) / 32;
+  st = launch_prologue(hdr, d_out_bits, (long long)res * res * W, o.accumulate ? 0 : 1, stream);
+  if (st != VOXTET_OK) return st;
+  DeviceInfo *dev = nullptr;
+  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+  if (n_verts > 0) {
+    k_load_fixed<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(d_xyz, n_verts, verts4, hdr);
+    g_launches.fetch_add(1);
+    if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
+  }
+  return run_voxelize(verts4, n_verts, d_tets, n_tets, res, k, d_out_bits, hdr, o, stream);
+}
+
+int voxtet_last_status(const void *d_workspace, void *stream_) {
+  if (!d_workspace) return VOXTET_ERR_WORKSPACE;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream_)) != cudaSuccess) return VOXTET_ERR_CUDA;
+  int bits = 0;
+  if (cudaMemcpy(&bits, &reinterpret_cast<const Header *>(d_workspace)->status_bits, sizeof(int),
+                 cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VOXTET_ERR_CUDA;
+  return map_status_bits(bits);
+}
+
+int voxtet_read_stats(const void *d_workspace, voxtet_stats *out, void *stream_) {
+  if (!d_workspace || !out) return VOXTET_ERR_ARG;
+  if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream_)) != cudaSuccess) return VOXTET_ERR_CUDA;
+  Header h;
+  if (cudaMemcpy(&h, d_workspace, sizeof(Header), cudaMemcpyDeviceToHost) != cudaSuccess) return VOXTET_ERR_CUDA;
+  std::memset(out, 0, sizeof(*out));
+  out->spans = h.spans;
+  out->rows = h.rows;
+  out->fallback_rows = h.fallback_rows;
+  out->degenerate_tets = h.degenerate;
+  out->wide_tets = h.wide;
+  if (t_prof.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(t_prof.stop) != cudaSuccess ||
+        cudaEventElapsedTime(&ms, t_prof.start, t_prof.stop) != cudaSuccess)
+      return VOXTET_ERR_CUDA;
+    out->kernel_ns = (uint64_t)((double)ms * 1.0e6);
+  }
+  return VOXTET_OK;
+}
+
+const char *voxtet_strerror(int s) {
+  switch (s) {
+    case VOXTET_OK: return "ok";
+    case VOXTET_ERR_ARG: return "invalid argument";
+    case VOXTET_ERR_RES: return "resolution must be a power of two in [1, VOXTET_MAX_RES]";
+    case VOXTET_ERR_INDEX: return "tetrahedron vertex index out of range";
+    case VOXTET_ERR_RANGE: return "snapped vertex coordinate beyond 2^21 lattice units";
+    case VOXTET_ERR_NAN: return "non-finite vertex coordinate";
+    case VOXTET_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case VOXTET_ERR_CUDA: return "CUDA runtime error";
+    case VOXTET_ERR_TIMEOUT: return "device-side wait timed out";
+    case VOXTET_ERR_NOMEM: return "arena too small";
+    default: return "unknown status";
+  }
+}
+
+uint64_t voxtet_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+"""Thin ctypes binding of the C ABI in include/voxtet.h (argument marshalling only).
+
+Every step of the voxelization runs in the CUDA library ``libvoxtet.so``; this
+module only turns torch tensors (device memory) and streams into the plain
+pointers and sizes the C entry points take.  There is no CPU fallback: if the
+library is missing or CUDA is unavailable, calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional, Sequence
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libvoxtet.so")
+
+OK = 0
+ERR_ARG, ERR_RES, ERR_INDEX, ERR_RANGE, ERR_NAN = -1, -2, -3, -4, -5
+ERR_WORKSPACE, ERR_CUDA, ERR_TIMEOUT, ERR_NOMEM = -6, -7, -8, -9
+MAX_RES = 8192
+
+# every symbol include/voxtet.h declares
+EXPORTED = (
+    "voxtet_default_opts", "voxtet_workspace_size", "voxelize_tets", "voxelize_tets_fixed",
+    "voxtet_last_status", "voxtet_read_stats", "voxtet_strerror", "voxtet_launch_count",
+)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("accumulate", ctypes.c_int32), ("use_filter", ctypes.c_int32),
+                ("sync", ctypes.c_int32), ("span_rows", ctypes.c_int32), ("block", ctypes.c_int32),
+                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("spans", ctypes.c_uint64), ("rows", ctypes.c_uint64), ("fallback_rows", ctypes.c_uint64),
+                ("degenerate_tets", ctypes.c_uint64), ("wide_tets", ctypes.c_uint64),
+                ("kernel_ns", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 2)]
+
+
+class VoxtetError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"voxtet status {status}: {msg or strerror(status)}")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: Optional[str] = None):
+    """Load (once) and return the CUDA library; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libvoxtet.so not built ({p}); run paper_2106_01326_gb300/build.py")
+        lib = ctypes.CDLL(p)
+        P, i64, i32, f32, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float, ctypes.c_size_t
+        lib.voxtet_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        lib.voxtet_default_opts.restype = None
+        lib.voxtet_workspace_size.argtypes = [i64, i64, i32]
+        lib.voxtet_workspace_size.restype = sz
+        lib.voxelize_tets.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, i32, P, P, sz,
+                                      ctypes.POINTER(Opts), P]
+        lib.voxelize_tets.restype = ctypes.c_int
+        lib.voxelize_tets_fixed.argtypes = [P, i64, P, i64, i32, P, P, sz, ctypes.POINTER(Opts), P]
+        lib.voxelize_tets_fixed.restype = ctypes.c_int
+        lib.voxtet_last_status.argtypes = [P, P]
+        lib.voxtet_last_status.restype = ctypes.c_int
+        lib.voxtet_read_stats.argtypes = [P, ctypes.POINTER(Stats), P]
+        lib.voxtet_read_stats.restype = ctypes.c_int
+        lib.voxtet_strerror.argtypes = [ctypes.c_int]
+        lib.voxtet_strerror.restype = ctypes.c_char_p
+        lib.voxtet_launch_count.argtypes = []
+        lib.voxtet_launch_count.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().voxtet_strerror(int(status)).decode()
+    except RuntimeError:
+        return "library not loaded"
+
+
+def launch_count() -> int:
+    return int(load().voxtet_launch_count())
+
+
+def grid_words(res: int) -> int:
+    return res * res * ((res + 31) // 32)
+
+
+def workspace_size(n_tets: int, n_verts: int, res: int) -> int:
+    return int(load().voxtet_workspace_size(int(n_tets), int(n_verts), int(res)))
+
+
+def make_opts(mode: int = 0, accumulate: bool = False, use_filter: bool = True, sync: bool = True,
+              span_rows: int = 0, block: int = 0, profile: bool = False) -> Opts:
+    o = Opts()
+    load().voxtet_default_opts(ctypes.byref(o))
+    o.mode, o.accumulate, o.use_filter, o.sync = int(mode), int(bool(accumulate)), int(bool(use_filter)), int(bool(sync))
+    o.span_rows, o.block, o.profile = int(span_rows), int(block), int(bool(profile))
+    return o
+
+
+def _torch():
+    import torch
+
+    return torch
+
+
+def _stream_ptr(stream) -> int:
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _check_cuda_tensor(t, name: str, dtype):
+    torch = _torch()
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+def alloc_grid(res: int, device=None):
+    """A grid buffer (int32 storage holding the uint32 bit words), shape [res, res, W]."""
+    torch = _torch()
+    return torch.empty((res, res, (res + 31) // 32), dtype=torch.int32, device=device or "cuda")
+
+
+def alloc_workspace(n_tets: int, n_verts: int, res: int, device=None):
+    torch = _torch()
+    return torch.empty(workspace_size(n_tets, n_verts, res), dtype=torch.uint8, device=device or "cuda")
+
+
+def voxelize(verts, tets, origin: Sequence[float], voxel_size: float, res: int, out=None, workspace=None,
+             mode: int = 0, accumulate: bool = False, use_filter: bool = True, sync: bool = True,
+             span_rows: int = 0, stream=None, raise_on_error: bool = True, profile: bool = False):
+    """Grid (int32 tensor [res, res, W] of uint32 bit words) of a world-space mesh.
+
+    verts: float32 CUDA [n_verts, 3]; tets: int32 CUDA [n_tets, 4].  Returns ``out``
+    (or (status, out) when ``raise_on_error`` is False).
+    """
+    torch = _torch()
+    lib = load()
+    _check_cuda_tensor(verts, "verts", torch.float32)
+    _check_cuda_tensor(tets, "tets", torch.int32)
+    n_v, n_t = verts.shape[0], tets.shape[0]
+    if out is None:
+        out = alloc_grid(res, verts.device)
+    _check_cuda_tensor(out, "out", torch.int32)
+    if workspace is None:
+        workspace = alloc_workspace(n_t, n_v, res, verts.device)
+    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile)
+    org = (ctypes.c_float * 3)(*[float(x) for x in origin])
+    st = lib.voxelize_tets(verts.data_ptr(), n_v, tets.data_ptr(), n_t, ctypes.byref(org), float(voxel_size),
+                           int(res), out.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(o),
+                           _stream_ptr(stream))
+    if raise_on_error:
+        if st != OK:
+            raise VoxtetError(st)
+        return out
+    return st, out
+
+
+def voxelize_fixed(xyz, tets, res: int, out=None, workspace=None, mode: int = 0, accumulate: bool = False,
+                   use_filter: bool = True, sync: bool = True, span_rows: int = 0, stream=None,
+                   raise_on_error: bool = True, profile: bool = False):
+    """Grid of a mesh whose vertices are already on the 2^20-per-grid lattice (int32 [n, 3])."""
+    torch = _torch()
+    lib = load()
+    _check_cuda_tensor(xyz, "xyz", torch.int32)
+    _check_cuda_tensor(tets, "tets", torch.int32)
+    n_v, n_t = xyz.shape[0], tets.shape[0]
+    if out is None:
+        out = alloc_grid(res, xyz.device)
+    _check_cuda_tensor(out, "out", torch.int32)
+    if workspace is None:
+        workspace = alloc_workspace(n_t, n_v, res, xyz.device)
+    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile)
+    st = lib.voxelize_tets_fixed(xyz.data_ptr(), n_v, tets.data_ptr(), n_t, int(res), out.data_ptr(),
+                                 workspace.data_ptr(), workspace.numel(), ctypes.byref(o), _stream_ptr(stream))
+    if raise_on_error:
+        if st != OK:
+            raise VoxtetError(st)
+        return out
+    return st, out
+
+
+def last_status(workspace, stream=None) -> int:
+    return int(load().voxtet_last_status(workspace.data_ptr(), _stream_ptr(stream)))
+
+
+def read_stats(workspace, stream=None) -> dict:
+    s = Stats()
+    st = load().voxtet_read_stats(workspace.data_ptr(), ctypes.byref(s), _stream_ptr(stream))
+    if st != OK:
+        raise VoxtetError(st)
+    return {"spans": s.spans, "rows": s.rows, "fallback_rows": s.fallback_rows,
+            "degenerate_tets": s.degenerate_tets, "wide_tets": s.wide_tets, "kernel_ns": s.kernel_ns}

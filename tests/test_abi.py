@@ -1,0 +1,79 @@
+"""The C-ABI library loads and exports every symbol include/voxtet.h declares.
+
+Host-only calls (no GPU): option defaults, workspace sizing, status strings and
+the argument checks that run before anything is launched.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2106_01326_gb300 import build as vbuild
+from paper_2106_01326_gb300 import voxtet as vt
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    vbuild.build()
+    return vt.load()
+
+
+def _declared_functions():
+    names = set()
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        for m in re.finditer(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\(", src, flags=re.M):
+            if m.group(1) not in ("if", "defined"):
+                names.add(m.group(1))
+    return names
+
+
+def test_exports_every_declared_symbol(lib):
+    declared = _declared_functions()
+    assert declared, "no declarations parsed"
+    assert declared == set(vt.EXPORTED)
+    for name in declared:
+        assert hasattr(lib, name), name
+
+
+def test_host_side_calls(lib):
+    o = vt.Opts()
+    lib.voxtet_default_opts(ctypes.byref(o))
+    assert (o.mode, o.accumulate, o.use_filter, o.sync, o.span_rows, o.block, o.profile) == (0, 0, 1, 1, 0, 0, 0)
+    assert vt.workspace_size(10, 100, 64) >= 256 + 16 * 100
+    assert vt.workspace_size(-1, 1, 64) == 0
+    assert vt.strerror(vt.ERR_INDEX) == "tetrahedron vertex index out of range"
+    assert vt.launch_count() >= 0
+
+
+def test_argument_checks_before_launch(lib):
+    """Invalid arguments are rejected on the host; fake non-null pointers are never touched."""
+    P = 1 << 20  # a 256-aligned fake address, never dereferenced
+    o = vt.make_opts()
+    org = (ctypes.c_float * 3)(0.0, 0.0, 0.0)
+    ws = vt.workspace_size(1, 4, 8)
+
+    def call(res=8, h=0.125, n_t=1, n_v=4, wsb=ws, tets=P, opts=o, out=P, work=P):
+        return lib.voxelize_tets(P, n_v, tets, n_t, ctypes.byref(org), h, res, out, work, wsb, ctypes.byref(opts), None)
+
+    assert call(res=12) == vt.ERR_RES
+    assert call(res=0) == vt.ERR_RES
+    assert call(res=vt.MAX_RES * 2) == vt.ERR_RES
+    assert call(h=0.0) == vt.ERR_ARG
+    assert call(h=float("nan")) == vt.ERR_ARG
+    assert call(n_t=-1) == vt.ERR_ARG
+    assert call(tets=P + 4) == vt.ERR_ARG  # tets must be 16-byte aligned
+    assert call(wsb=ws - 1) == vt.ERR_WORKSPACE
+    assert call(work=P + 16) == vt.ERR_WORKSPACE
+    assert call(out=0) == vt.ERR_ARG
+    bad = vt.make_opts(mode=2)
+    assert call(opts=bad) == vt.ERR_ARG
+    bad = vt.make_opts(block=96)
+    assert call(opts=bad) == vt.ERR_ARG
+    assert lib.voxelize_tets_fixed(P, 4, P, 1, 7, P, P, ws, ctypes.byref(o), None) == vt.ERR_RES

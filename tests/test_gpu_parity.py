@@ -1,0 +1,292 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit for bit.
+
+Small and medium cases are compared element by element over the whole grid;
+the full-size single-mesh workloads, in the launch configuration the benchmark
+times, are compared on sampled z-slabs the oracle computes directly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2106_01326_gb300 import meshgen as mg
+
+pytestmark = pytest.mark.gpu
+
+L = 1 << 20
+
+
+@pytest.fixture(scope="module")
+def vt():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2106_01326_gb300 import build as vbuild
+    from paper_2106_01326_gb300 import voxtet
+
+    vbuild.build()
+    oracle.build()
+    voxtet.load()
+    return voxtet
+
+
+def _dev(a, dtype):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype)
+
+
+def gpu_fixed(vt, xyz, tets, res, **kw):
+    import torch
+
+    g = vt.voxelize_fixed(_dev(xyz, torch.int32), _dev(tets.reshape(-1, 4), torch.int32), res, **kw)
+    return g.cpu().numpy().view(np.uint32)
+
+
+def gpu_world(vt, verts, tets, origin, h, res, **kw):
+    import torch
+
+    g = vt.voxelize(_dev(verts, torch.float32), _dev(tets.reshape(-1, 4), torch.int32), origin, h, res, **kw)
+    return g.cpu().numpy().view(np.uint32)
+
+
+def assert_same(got, ref, res, what=""):
+    got = np.asarray(got).view(np.uint32).reshape(ref.shape)
+    if np.array_equal(got, ref):
+        return
+    a, b = oracle.unpack(got, res), oracle.unpack(ref, ref.shape[1])
+    bad = np.argwhere(a != b)
+    l, j, i = bad[0]
+    raise AssertionError(f"{what}: {len(bad)} samples differ; first (i={i}, j={j}, l={l}): gpu={a[l, j, i]} "
+                         f"oracle={b[l, j, i]}")
+
+
+def s_of(res):
+    return 1 << (19 - (res.bit_length() - 1))
+
+
+def random_soup(rng, n_tets, res, spread=1.0, tie_frac=0.3, lo=-0.15, hi=1.15):
+    s = s_of(res)
+    c = rng.uniform(lo, hi, size=(n_tets, 1, 3)) * L
+    size = rng.uniform(0.02, 0.5, size=(n_tets, 1, 1)) * L * spread
+    pts = c + rng.uniform(-1, 1, size=(n_tets, 4, 3)) * size
+    xyz = np.clip(np.rint(pts), -(1 << 21), 1 << 21).astype(np.int64).reshape(-1, 3)
+    mask = rng.random(size=xyz.shape) < tie_frac
+    on_plane = (np.rint(xyz / (2 * s)) * 2 + 1) * s
+    xyz = np.where(mask, np.clip(on_plane, -(1 << 21), 1 << 21), xyz).astype(np.int32)
+    tets = np.arange(len(xyz), dtype=np.int32).reshape(n_tets, 4)
+    return xyz, tets
+
+
+# ------------------------------------------------------------------ small, whole grid
+
+@pytest.mark.parametrize("use_filter", [True, False])
+@pytest.mark.parametrize("span_rows", [1, 16, 4096])
+def test_plain_lattice_world_coords(vt, use_filter, span_rows):
+    c = mg.single_mesh_config("plain_8")
+    ref = oracle.voxelize(c["verts"], c["tets"], c["origin"], c["voxel_size"], c["res"])
+    got = gpu_world(vt, c["verts"], c["tets"], c["origin"], c["voxel_size"], c["res"], use_filter=use_filter,
+                    span_rows=span_rows)
+    assert_same(got, ref, c["res"], "plain_8")
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_random_soup_all_modes(vt, seed):
+    rng = np.random.default_rng(1000 + seed)
+    res = [1, 2, 4, 8, 16, 32, 64, 128, 256, 32, 64, 16][seed]
+    xyz, tets = random_soup(rng, 60 + 20 * seed, res)
+    for mode in (0, 1):
+        ref = oracle.voxelize_fixed(xyz, tets, res, mode=mode)
+        for use_filter in (True, False):
+            got = gpu_fixed(vt, xyz, tets, res, mode=mode, use_filter=use_filter, span_rows=1 + seed % 5)
+            assert_same(got, ref, res, f"soup seed={seed} res={res} mode={mode} filter={use_filter}")
+
+
+@pytest.mark.parametrize("res", [16, 64, 128])
+def test_unjittered_lattice_ties(vt, res):
+    """Every shared Kuhn face passes through samples; many faces are parallel to x."""
+    for N, off in [(4, 0), (8, 3 * s_of(res)), (5, 2 * s_of(res))]:
+        ijk, tets = mg.kuhn_lattice_int(N)
+        xyz = (ijk * (L // N) + off).astype(np.int32)
+        for mode in (0, 1):
+            ref = oracle.voxelize_fixed(xyz, tets, res, mode=mode)
+            got = gpu_fixed(vt, xyz, tets, res, mode=mode)
+            assert_same(got, ref, res, f"lattice N={N} off={off} mode={mode}")
+
+
+def test_wide_tets_128bit_path(vt):
+    """Tets wider than 2^20 lattice units take the 128-bit exact path."""
+    rng = np.random.default_rng(7)
+    for res in (8, 32, 128):
+        xyz, tets = random_soup(rng, 40, res, spread=4.0, lo=-0.5, hi=1.5)
+        for mode in (0, 1):
+            ref = oracle.voxelize_fixed(xyz, tets, res, mode=mode)
+            got = gpu_fixed(vt, xyz, tets, res, mode=mode)
+            assert_same(got, ref, res, f"wide res={res} mode={mode}")
+    # the extreme corners of the coordinate range
+    C = 1 << 21
+    xyz = np.array([[-C, -C, -C], [C, -C, -C], [-C, C, -C], [-C, -C, C], [C, C, C]], dtype=np.int32)
+    tets = np.array([[0, 1, 2, 3], [4, 1, 2, 3], [1, 2, 3, 4]], dtype=np.int32)
+    ref = oracle.voxelize_fixed(xyz, tets, 32)
+    assert_same(gpu_fixed(vt, xyz, tets, 32), ref, 32, "corners")
+
+
+def test_slivers_and_degenerates(vt):
+    v, t = mg.kuhn_lattice(12, 0.25, 5)
+    v, t, _ = mg.add_slivers(v, t, 0.05, 6, d_lattice_units=range(0, 9))
+    res = 128
+    for mode in (0, 1):
+        ref = oracle.voxelize(v, t, (0, 0, 0), 1 / res, res, mode=mode)
+        got = gpu_world(vt, v, t, (0, 0, 0), 1 / res, res, mode=mode)
+        assert_same(got, ref, res, f"slivers mode={mode}")
+    flat = np.array([[0, 0, 0], [L, 0, 0], [0, L, 0], [L // 2, L // 2, 0]], dtype=np.int32)
+    got = gpu_fixed(vt, flat, np.array([[0, 1, 2, 3]], np.int32), 16)
+    assert not got.any()
+
+
+def test_world_coords_general_origin_and_voxel_size(vt):
+    """Non-power-of-two voxel size (double division in the snap) and an offset origin."""
+    v, t = mg.kuhn_lattice(6, 0.3, 8)
+    v = (v * 1.7 - 0.35).astype(np.float32)
+    for origin, h, res in [((-0.4, -0.3, -0.35), 1.6 / 64, 64), ((0.1, 0.2, -0.1), 0.0123, 128),
+                           ((-0.5, -0.5, -0.5), 0.125, 16)]:
+        st, _ = oracle.snap(v, origin, h, res)
+        if st != 0:
+            continue
+        ref = oracle.voxelize(v, t, origin, h, res)
+        got = gpu_world(vt, v, t, origin, h, res)
+        assert_same(got, ref, res, f"origin={origin} h={h}")
+
+
+def test_accumulate_ors_into_existing_grid(vt):
+    import torch
+
+    rng = np.random.default_rng(3)
+    res = 64
+    xa, ta = random_soup(rng, 30, res)
+    xb, tb = random_soup(rng, 30, res)
+    ref = oracle.voxelize_fixed(xa, ta, res) | oracle.voxelize_fixed(xb, tb, res)
+    g = vt.voxelize_fixed(_dev(xa, torch.int32), _dev(ta, torch.int32), res)
+    vt.voxelize_fixed(_dev(xb, torch.int32), _dev(tb, torch.int32), res, out=g, accumulate=True)
+    assert_same(g.cpu().numpy(), ref, res, "accumulate")
+
+
+def test_shuffle_and_duplicates_idempotent(vt):
+    """Lost or racing OR writes would show up as order dependence."""
+    c = mg.single_mesh_config("torus_48")
+    rng = np.random.default_rng(0)
+    t = c["tets"]
+    base = gpu_world(vt, c["verts"], t, (0, 0, 0), 1 / 256, 256)
+    shuf = np.concatenate([t, t[rng.permutation(len(t))[: len(t) // 3]]])[rng.permutation(len(t) + len(t) // 3)]
+    got = gpu_world(vt, c["verts"], shuf, (0, 0, 0), 1 / 256, 256)
+    assert np.array_equal(base, got)
+
+
+def test_empty_and_tiny_inputs(vt):
+    import torch
+
+    g = vt.voxelize_fixed(torch.zeros((0, 3), dtype=torch.int32, device="cuda"),
+                          torch.zeros((0, 4), dtype=torch.int32, device="cuda"), 64)
+    assert int(torch.count_nonzero(g)) == 0
+    # res = 1: one sample at the grid centre
+    xyz = np.array([[0, 0, 0], [L, 0, 0], [0, L, 0], [0, 0, L]], dtype=np.int32)
+    assert gpu_fixed(vt, xyz, np.array([[0, 1, 2, 3]], np.int32), 1).ravel()[0] == 0  # centre outside corner tet
+    xyz2 = np.array([[0, 0, 0], [L, 0, 0], [L, L, 0], [L, L, L]], dtype=np.int32)
+    assert gpu_fixed(vt, xyz2, np.array([[0, 1, 2, 3]], np.int32), 1).ravel()[0] == 1  # on the diagonal: closed
+
+
+def test_error_statuses(vt):
+    import torch
+
+    v = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [0, 0, 1]], dtype=np.float32)
+    t = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    dv = lambda a: _dev(a, torch.float32)
+    dt = lambda a: _dev(a, torch.int32)
+    bad = v.copy()
+    bad[1, 2] = np.inf
+    st, _ = vt.voxelize(dv(bad), dt(t), (0, 0, 0), 0.25, 4, raise_on_error=False)
+    assert st == vt.ERR_NAN
+    far = v.copy()
+    far[2, 0] = 5.0
+    st, _ = vt.voxelize(dv(far), dt(t), (0, 0, 0), 0.25, 4, raise_on_error=False)
+    assert st == vt.ERR_RANGE
+    st, _ = vt.voxelize(dv(v), dt(np.array([[0, 1, 2, 9]], np.int32)), (0, 0, 0), 0.25, 4, raise_on_error=False)
+    assert st == vt.ERR_INDEX
+    st, _ = vt.voxelize(dv(v), dt(np.array([[0, -3, 2, 1]], np.int32)), (0, 0, 0), 0.25, 4, raise_on_error=False)
+    assert st == vt.ERR_INDEX
+    xyz = np.array([[0, 0, 0], [(1 << 21) + 1, 0, 0], [0, L, 0], [0, 0, L]], dtype=np.int32)
+    st, _ = vt.voxelize_fixed(dt(xyz), dt(t), 8, raise_on_error=False)
+    assert st == vt.ERR_RANGE
+    # asynchronous form: the status is read afterwards from the workspace
+    ws = vt.alloc_workspace(1, 4, 4)
+    st, _ = vt.voxelize(dv(bad), dt(t), (0, 0, 0), 0.25, 4, workspace=ws, sync=False, raise_on_error=False)
+    assert st == vt.OK
+    assert vt.last_status(ws) == vt.ERR_NAN
+    # a clean call afterwards on the same workspace reports OK again
+    st, _ = vt.voxelize(dv(v), dt(t), (0, 0, 0), 0.25, 4, workspace=ws, raise_on_error=False)
+    assert st == vt.OK
+
+
+# ------------------------------------------------------------------ medium, whole grid
+
+def test_torus_48_full_grid(vt):
+    c = mg.single_mesh_config("torus_48")
+    ref = oracle.voxelize(c["verts"], c["tets"], c["origin"], c["voxel_size"], c["res"])
+    got = gpu_world(vt, c["verts"], c["tets"], c["origin"], c["voxel_size"], c["res"])
+    assert_same(got, ref, c["res"], "torus_48")
+
+
+# ------------------------------------------------------------------ full size, sampled slabs
+
+def _slab_check(vt, name, n_slabs, depth, seed):
+    import torch
+
+    c = mg.single_mesh_config(name)
+    res = c["res"]
+    verts, tets = c["verts"], c["tets"]
+    ws = vt.alloc_workspace(len(tets), len(verts), res)
+    g = vt.voxelize(_dev(verts, torch.float32), _dev(tets, torch.int32), c["origin"], c["voxel_size"], res,
+                    workspace=ws)
+    stats = vt.read_stats(ws)
+    st, xyz = oracle.snap(verts, c["origin"], c["voxel_size"], res)
+    assert st == 0
+    rng = np.random.default_rng(seed)
+    starts = sorted(set([0, res - depth] + list(rng.integers(0, res - depth, size=n_slabs - 2))))
+    for z0 in starts:
+        ref = oracle.voxelize_fixed_slab(xyz, tets, res, int(z0), int(z0) + depth)
+        got = g[z0:z0 + depth].cpu().numpy().view(np.uint32)
+        if not np.array_equal(got, ref):
+            a, b = oracle.unpack(got.reshape(depth * res, res, -1), res), oracle.unpack(
+                ref.reshape(depth * res, res, -1), res)
+            raise AssertionError(f"{name}: slab z0={z0} differs in {(a != b).sum()} samples")
+    return stats
+
+
+def test_full_size_sliver_60_at_512(vt):
+    stats = _slab_check(vt, "sliver_60", n_slabs=6, depth=3, seed=1)
+    assert stats["degenerate_tets"] > 0  # snapped slivers that became exactly flat
+    assert stats["rows"] > 0
+    assert stats["fallback_rows"] < 0.01 * stats["rows"]
+
+
+def test_full_size_sliver_60_at_1024(vt):
+    _slab_check(vt, "sliver_60_1024", n_slabs=4, depth=2, seed=2)
+
+
+def test_max_resolution_sampled(vt):
+    """res = 8192 (a 64 GiB grid): a few tets, checked on the slabs they touch; the rest stays zero."""
+    import torch
+
+    res = 8192
+    rng = np.random.default_rng(11)
+    xyz, tets = random_soup(rng, 6, res, spread=0.01, lo=0.3, hi=0.32)
+    g = vt.voxelize_fixed(_dev(xyz, torch.int32), _dev(tets, torch.int32), res)
+    s = s_of(res)
+    zmin = max(0, int((xyz[:, 2].min() - s) // (2 * s)))
+    zmax = min(res, int((xyz[:, 2].max() - s) // (2 * s)) + 2)
+    ref = oracle.voxelize_fixed_slab(xyz, tets, res, zmin, zmax)
+    got = g[zmin:zmax].cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, ref)
+    assert int(torch.count_nonzero(g[:zmin])) == 0 and int(torch.count_nonzero(g[zmax:])) == 0
+    del g
+    torch.cuda.empty_cache()
