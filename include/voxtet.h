@@ -72,10 +72,10 @@ typedef struct {
     int32_t accumulate; /* 0 = clear out_bits first (default), 1 = OR into its current contents */
     int32_t use_filter; /* 1 = single-precision filter + exact fallback (default), 0 = exact integer only */
     int32_t sync;       /* 1 = synchronize the stream and return device-detected status (default 1) */
-    int32_t span_rows;  /* x-rows per work item of the scanline kernel; 0 = automatic */
+    int32_t span_rows;  /* bounding-box x-rows per work item (whole z-slices); 0 = automatic */
     int32_t block;      /* threads per block of the scanline kernel; 0 = automatic (only 256 is accepted) */
     int32_t profile;    /* 1 = record CUDA events around the main kernel on `stream` (see voxtet_stats) */
-    int32_t reserved;
+    int32_t row_cull;   /* skip x-rows outside each z-slice's cross-section: 0 = automatic, 1 = on, 2 = off */
 } voxtet_opts;
 
 /* Counters the last call on a workspace left in it (read with voxtet_read_stats). */

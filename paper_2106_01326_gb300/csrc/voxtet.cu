@@ -33,9 +33,13 @@
 
 namespace voxtet {
 
-constexpr int kBlock = 256;              // threads per block == tets per tile
-constexpr int kMaxSpansPerTet = 1 << 22; // keeps a tile's span count within 32 bits
-constexpr int kDefaultSpanRows = 16;
+#ifndef VOXTET_MIN_BLOCKS
+#define VOXTET_MIN_BLOCKS 2  // resident blocks per SM the register budget is sized for
+#endif
+
+constexpr int kBlock = 256;             // threads per block
+constexpr int kDefaultSpanRows = 128;   // bounding-box rows per span (whole z-slices)
+constexpr int kCullMinRes = 256;        // automatic row culling from this resolution up
 
 // Workspace header (first 256 bytes of the workspace).
 struct Header {
@@ -51,16 +55,6 @@ struct Header {
 };
 static_assert(sizeof(Header) == 256, "header is 256 bytes");
 
-// Per-tet record staged in shared memory for the span phase.
-struct __align__(16) TetRec {
-  float alpha[4], beta[4], gamma[4], delta[4];  // filter data, slot order
-  Exact<i64> X;                                 // exact data, slot order
-  int i0, j0, l0, na;
-  int nb, nc, meta, rows_per_span;  // meta: nup | nlo << 4 | wide << 8
-  long long tet;
-  long long pad;
-};
-
 struct Params {
   const int4 *verts4;
   const int4 *tets;
@@ -71,7 +65,7 @@ struct Params {
   int res;
   int W;
   int sh;          // 20 - log2(res)
-  int span_rows;
+  int span_rows;   // target bounding-box rows per span
 };
 
 // ------------------------------------------------------------------ small kernels
@@ -159,169 +153,237 @@ __device__ __forceinline__ void or_span(uint32_t *__restrict__ row, int x0, int 
   else atomicOr(row + w1, m1);
 }
 
-// ------------------------------------------------------------------ tet setup (phase 1)
+// ------------------------------------------------------------------ per-tet helpers
 
-__device__ __forceinline__ void load_tet_vertices(const Params &p, const int4 q, int3 V[4], int &flags) {
+// Loads tet t; false if an index is out of range (recorded) or a vertex failed its snap
+// (already recorded by the snap kernel).
+__device__ __forceinline__ bool load_tet(const Params &p, long long t, int3 V[4], int &err) {
+  const int4 q = p.tets[t];
+  const unsigned long long nv = (unsigned long long)p.n_verts;
+  if (q.x < 0 || q.y < 0 || q.z < 0 || q.w < 0 || (unsigned long long)q.x >= nv || (unsigned long long)q.y >= nv ||
+      (unsigned long long)q.z >= nv || (unsigned long long)q.w >= nv) {
+    err |= kErrIndex;
+    return false;
+  }
   const int4 A = p.verts4[q.x], B = p.verts4[q.y], C = p.verts4[q.z], D = p.verts4[q.w];
   V[0] = make_int3(A.x, A.y, A.z);
   V[1] = make_int3(B.x, B.y, B.z);
   V[2] = make_int3(C.x, C.y, C.z);
   V[3] = make_int3(D.x, D.y, D.z);
-  flags = A.w | B.w | C.w | D.w;
+  return (A.w | B.w | C.w | D.w) == 0;
 }
 
-// Fills rec for tet t and returns its span count (0 if it marks nothing).
-template <bool FILTER>
-__device__ uint32_t setup_tet(const Params &p, long long t, TetRec &rec, int &err, unsigned &n_degenerate,
-                              unsigned &n_wide) {
-  const int4 q = p.tets[t];
-  const unsigned long long nv = (unsigned long long)p.n_verts;
-  if ((unsigned long long)(unsigned)q.x >= nv || (unsigned long long)(unsigned)q.y >= nv ||
-      (unsigned long long)(unsigned)q.z >= nv || (unsigned long long)(unsigned)q.w >= nv || q.x < 0 || q.y < 0 ||
-      q.z < 0 || q.w < 0) {
-    err |= kErrIndex;
-    return 0;
-  }
+// z-slices per span: about span_rows bounding-box rows per work item.
+__device__ __forceinline__ int slices_per_span(const Params &p, int nb) {
+  const int S = p.span_rows / nb;
+  return S < 1 ? 1 : S;
+}
+
+// Phase (1): sample box, orientation and span count of tet t (0 if it marks nothing).
+__device__ uint32_t count_spans(const Params &p, long long t, int &err, unsigned &n_degenerate,
+                                unsigned &n_wide) {
   int3 V[4];
-  int flags;
-  load_tet_vertices(p, q, V, flags);
-  if (flags) return 0;  // a vertex failed the snap; its error is already recorded
+  if (!load_tet(p, t, V, err)) return 0;
   Box bx;
   const int E = tet_box(V, p.sh, p.res, bx);
-  const int sg = v6_sign(V, E);
-  if (sg == 0) {
+  if (v6_sign(V, E) == 0) {
     ++n_degenerate;
     return 0;
   }
   if (bx.na <= 0 || bx.nb <= 0 || bx.nc <= 0) return 0;
-  if (sg < 0) {
-    const int3 tmp = V[2];
-    V[2] = V[3];
-    V[3] = tmp;
-  }
-  const uint32_t rows = (uint32_t)bx.nb * (uint32_t)bx.nc;
-  uint32_t R = (uint32_t)p.span_rows;
-  const uint32_t need = (rows + kMaxSpansPerTet - 1) / kMaxSpansPerTet;
-  if (R < need) R = need;
-  rec.i0 = bx.i0;
-  rec.j0 = bx.j0;
-  rec.l0 = bx.l0;
-  rec.na = bx.na;
-  rec.nb = bx.nb;
-  rec.nc = bx.nc;
-  rec.rows_per_span = (int)R;
-  rec.tet = t;
-  if (E <= kNarrowExtent) {
-    Exact<i64> X;
-    exact_setup<i64>(V, bx, p.sh, X);
-    int slot[4], nup = 0, nlo = 0;
-    slot_order<i64>(X, slot, nup, nlo);
-    const float fb = (float)(bx.nb - 1), fc = (float)(bx.nc - 1);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int q = slot[m];
-      rec.X.L[q] = X.L[m];
-      rec.X.Dx[q] = X.Dx[m];
-      rec.X.Dy[q] = X.Dy[m];
-      rec.X.Dz[q] = X.Dz[m];
-      if (FILTER && X.Dx[m] != 0) {
-        float a, b, g, d;
-        filter_slot(X.L[m], X.Dx[m], X.Dy[m], X.Dz[m], fb, fc, a, b, g, d);
-        rec.alpha[q] = a;
-        rec.beta[q] = b;
-        rec.gamma[q] = g;
-        rec.delta[q] = d;
-      }
-    }
-    rec.meta = nup | (nlo << 4);
-  } else {
-    rec.meta = 1 << 8;
-    ++n_wide;
-  }
-  return (rows + R - 1) / R;
+  if (E > kNarrowExtent) ++n_wide;
+  const int S = slices_per_span(p, bx.nb);
+  return (uint32_t)((bx.nc + S - 1) / S);
 }
 
-// ------------------------------------------------------------------ span phase
-
-struct RowCounters {
-  unsigned rows = 0, fallback = 0;
-};
-
-// Tets wider than 2^20 lattice units: 128-bit exact arithmetic for every row.
-template <bool STRICT>
-__device__ __noinline__ void span_wide(const Params &p, const TetRec &rec, uint32_t r0, uint32_t r1,
-                                       RowCounters &ctr) {
-  const int4 q = p.tets[rec.tet];
-  int3 V[4];
-  int flags;
-  load_tet_vertices(p, q, V, flags);
-  Box bx;
+// Loads, orients (V6 > 0) and boxes a tet already known to be live.
+__device__ __forceinline__ int oriented_tet(const Params &p, long long t, int3 V[4], Box &bx) {
+  int dummy = 0;
+  load_tet(p, t, V, dummy);
   const int E = tet_box(V, p.sh, p.res, bx);
   if (v6_sign(V, E) < 0) {
     const int3 tmp = V[2];
     V[2] = V[3];
     V[3] = tmp;
   }
-  Exact<i128> X;
-  exact_setup<i128>(V, bx, p.sh, X);
+  return E;
+}
+
+struct RowCounters {
+  unsigned rows = 0, fallback = 0;
+};
+
+// Exact interval of row (b, c) of tet t, recomputed from scratch (the filter's rare
+// uncertain rows; 64-bit exact arithmetic, the tet is narrow).
+template <bool STRICT>
+__device__ __noinline__ bool exact_row_of_tet(const Params &p, long long t, int b, int c, int &lo, int &hi) {
+  int3 V[4];
+  Box bx;
+  oriented_tet(p, t, V, bx);
+  Exact<i64> X;
+  exact_setup<i64>(V, bx, p.sh, X);
   int slot[4], nup = 0, nlo = 0;
-  slot_order<i128>(X, slot, nup, nlo);
-  permute_slots<i128>(X, slot);
-  const int nb = rec.nb;
-  for (uint32_t r = r0; r < r1; ++r) {
-    const int c = (int)(r / (uint32_t)nb), b = (int)(r - (uint32_t)c * nb);
-    int lo, hi;
-    ++ctr.rows;
-    if (exact_row<STRICT, i128>(X, nup, nlo, rec.na, b, c, lo, hi)) {
-      uint32_t *row = p.out + ((size_t)(rec.l0 + c) * p.res + (rec.j0 + b)) * p.W;
-      or_span(row, rec.i0 + lo, rec.i0 + hi);
+  slot_order<i64>(X, slot, nup, nlo);
+  permute_slots<i64>(X, slot);
+  return exact_row<STRICT, i64>(X, nup, nlo, bx.na, b, c, lo, hi);
+}
+
+// Tets wider than 2^20 lattice units, and the exact-only mode: every bounding-box row
+// of slices [c0, c1) solved with exact integers of type T.
+template <bool STRICT, typename T>
+__device__ __noinline__ void span_exact(const Params &p, long long t, int c0, int c1, RowCounters &ctr) {
+  int3 V[4];
+  Box bx;
+  oriented_tet(p, t, V, bx);
+  Exact<T> X;
+  exact_setup<T>(V, bx, p.sh, X);
+  int slot[4], nup = 0, nlo = 0;
+  slot_order<T>(X, slot, nup, nlo);
+  permute_slots<T>(X, slot);
+  for (int c = c0; c < c1; ++c) {
+    uint32_t *row = p.out + ((size_t)(bx.l0 + c) * p.res + bx.j0) * p.W;
+    for (int b = 0; b < bx.nb; ++b, row += p.W) {
+      int lo, hi;
+      ++ctr.rows;
+      if (exact_row<STRICT, T>(X, nup, nlo, bx.na, b, c, lo, hi)) or_span(row, bx.i0 + lo, bx.i0 + hi);
     }
   }
 }
 
-template <bool STRICT, bool FILTER>
-__device__ __forceinline__ void span_rows(const Params &p, const TetRec &rec, uint32_t r0, uint32_t r1,
-                                          RowCounters &ctr) {
-  const int meta = rec.meta;
-  if (meta >> 8) {
-    span_wide<STRICT>(p, rec, r0, r1, ctr);
+// Rows of slice c that can hold samples: the y-extent of the tet's cross-section at
+// the slice's z, from the crossing points of its 6 edges, widened by 2 lattice units
+// (the float error of each crossing point is below 0.7 units: |t - t~| <= 2.01u and
+// |y| < 2^22), so the range is a superset of the non-empty rows.
+__device__ __forceinline__ void slice_rows(const int3 V[4], const float rz[6], int Z, int s, int sh, int j0, int nb,
+                                           int &b_lo, int &b_hi) {
+  float ymin = 3.0e38f, ymax = -3.0e38f;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const int pi = e < 3 ? 0 : (e < 5 ? 1 : 2);
+    const int qi = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+    const int zp = V[pi].z, zq = V[qi].z;
+    const bool cross = zp != zq && min(zp, zq) <= Z && Z <= max(zp, zq);
+    if (cross) {
+      const float tpar = (float)(Z - zp) * rz[e];
+      const float y = __fmaf_rn(tpar, (float)(V[qi].y - V[pi].y), (float)V[pi].y);
+      ymin = fminf(ymin, y);
+      ymax = fmaxf(ymax, y);
+    }
+  }
+  if (ymin > ymax) {  // cannot happen for a slice inside the box; be safe
+    b_lo = 0;
+    b_hi = nb - 1;
     return;
   }
-  const int nup = meta & 7, nlo = (meta >> 4) & 7, nf = nup + nlo;
-  const int na = rec.na, nb = rec.nb;
-  float be[4], de[4], ac[4];
-  i64 Lc[4];
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    be[m] = rec.beta[m];
-    de[m] = rec.delta[m];
+  const int ylo = (int)floorf(ymin) - 2, yhi = (int)ceilf(ymax) + 2;
+  const int jlo = (ylo + s - 1) >> sh, jhi = (yhi - s) >> sh;
+  b_lo = max(jlo - j0, 0);
+  b_hi = min(jhi - j0, nb - 1);
+}
+
+// Rows allowed by a constraint with Dx == 0 (lam = H0 + Dy b for the slice), exact:
+// narrows [b_lo, b_hi] by bisection on the monotone lam(b).
+template <bool STRICT>
+__device__ __forceinline__ void narrow_by_row_constraint(i64 H0, i64 Dy, int &b_lo, int &b_hi) {
+  if (b_lo > b_hi) return;
+  if (Dy == 0) {
+    if (!lam_ok<STRICT, i64>(H0)) b_hi = b_lo - 1;
+    return;
   }
-  int c = (int)(r0 / (uint32_t)nb);
-  int b = (int)(r0 - (uint32_t)c * nb);
-  auto set_slice = [&](int cc) {
-    const float cf = (float)cc;
+  if (Dy > 0) {  // increasing: smallest b in [b_lo, b_hi + 1] that is ok
+    int x = b_lo, y = b_hi + 1;
+    while (x < y) {
+      const int mid = (x + y) >> 1;
+      if (lam_ok<STRICT, i64>(H0 + Dy * (i64)mid)) y = mid;
+      else x = mid + 1;
+    }
+    b_lo = x;
+  } else {  // decreasing: largest b in [b_lo - 1, b_hi] that is ok
+    int x = b_lo - 1, y = b_hi;
+    while (x < y) {
+      const int mid = (x + y + 1) >> 1;
+      if (lam_ok<STRICT, i64>(H0 + Dy * (i64)mid)) x = mid;
+      else y = mid - 1;
+    }
+    b_hi = x;
+  }
+}
+
+// Rows of slice c allowed by the (at most two) faces parallel to the x axis, whose
+// constraints do not depend on a.  Rare in general meshes, so the exact data is
+// recomputed here rather than kept live across the row loop.
+template <bool STRICT>
+__device__ __noinline__ void narrow_by_faces_parallel_to_x(const int3 V[4], const Box &bx, int sh, int c, int &b_lo,
+                                                           int &b_hi) {
+  Exact<i64> X;
+  exact_setup<i64>(V, bx, sh, X);
+#pragma unroll
+  for (int m = 0; m < 4; ++m)
+    if (X.Dx[m] == 0) narrow_by_row_constraint<STRICT>(X.L[m] + X.Dz[m] * (i64)c, X.Dy[m], b_lo, b_hi);
+}
+
+// Phase (3)+(4): slices [c0, c1) of tet t.
+template <bool STRICT, bool FILTER, bool YRANGE>
+__device__ __forceinline__ void run_span(const Params &p, long long t, int c0, int c1, RowCounters &ctr) {
+  int3 V[4];
+  Box bx;
+  const int E = oriented_tet(p, t, V, bx);
+  if (E > kNarrowExtent) {
+    span_exact<STRICT, i128>(p, t, c0, c1, ctr);
+    return;
+  }
+  if (!FILTER) {
+    span_exact<STRICT, i64>(p, t, c0, c1, ctr);
+    return;
+  }
+  float al[4], be[4], ga[4], de[4];
+  unsigned fmask = 0, umask = 0;
+  {
+    Exact<i64> X;
+    exact_setup<i64>(V, bx, p.sh, X);
+    const float fb = (float)(bx.nb - 1), fc = (float)(bx.nc - 1);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      if (FILTER) ac[m] = __fmaf_rn(rec.gamma[m], cf, rec.alpha[m]);
-      if (m >= nf) Lc[m] = rec.X.L[m] + rec.X.Dz[m] * (i64)cc;  // whole-row slots only
+      al[m] = be[m] = ga[m] = de[m] = 0.f;
+      if (X.Dx[m] != 0) {
+        fmask |= 1u << m;
+        if (X.Dx[m] < 0) umask |= 1u << m;
+        filter_slot(X.L[m], X.Dx[m], X.Dy[m], X.Dz[m], fb, fc, al[m], be[m], ga[m], de[m]);
+      }
     }
-  };
-  set_slice(c);
-  uint32_t *row = p.out + ((size_t)(rec.l0 + c) * p.res + (rec.j0 + b)) * p.W;
-  const float fhi0 = (float)(na - 1);
-  for (uint32_t r = r0; r < r1; ++r) {
-    int lo_i = 0, hi_i = -1;
-    bool ok;
-    if (FILTER) {
+  }
+  float rz[6];
+  if (YRANGE) {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      const int pi = e < 3 ? 0 : (e < 5 ? 1 : 2);
+      const int qi = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
+      const int dz = V[qi].z - V[pi].z;
+      rz[e] = dz != 0 ? __frcp_rn((float)dz) : 0.f;
+    }
+  }
+  const int s = 1 << (p.sh - 1);
+  const float fhi0 = (float)(bx.na - 1);
+  for (int c = c0; c < c1; ++c) {
+    int b_lo = 0, b_hi = bx.nb - 1;
+    if (YRANGE) slice_rows(V, rz, s + ((bx.l0 + c) << p.sh), s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
+    if (fmask != 0xFu) narrow_by_faces_parallel_to_x<STRICT>(V, bx, p.sh, c, b_lo, b_hi);
+    const float cf = (float)c;
+    float ac[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) ac[m] = __fmaf_rn(ga[m], cf, al[m]);
+    uint32_t *row = p.out + ((size_t)(bx.l0 + c) * p.res + (bx.j0 + b_lo)) * p.W;
+    for (int b = b_lo; b <= b_hi; ++b, row += p.W) {
+      ++ctr.rows;
       const float bf = (float)b;
       float lo = 0.f, hi = fhi0;
       bool amb = false;
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
-        if (m < nf) {
-          const float t = __fmaf_rn(be[m], bf, ac[m]);
-          const float tl = __fsub_rd(t, de[m]);
-          const float th = __fadd_ru(t, de[m]);
+        if ((fmask >> m) & 1u) {
+          const float tt = __fmaf_rn(be[m], bf, ac[m]);
+          const float tl = __fsub_rd(tt, de[m]);
+          const float th = __fadd_ru(tt, de[m]);
           float v;
           if (STRICT) {
             const float cc = ceilf(tl);
@@ -332,48 +394,36 @@ __device__ __forceinline__ void span_rows(const Params &p, const TetRec &rec, ui
             amb |= f > tl;
             v = f;
           }
-          if (m < nup) hi = fminf(hi, v);
+          if ((umask >> m) & 1u) hi = fminf(hi, v);
           else lo = fmaxf(lo, -v);
         }
       }
-      ok = lo <= hi;
-      if (nf < 4) {
-#pragma unroll
-        for (int m = 0; m < 4; ++m)
-          if (m >= nf) ok = ok && lam_ok<STRICT, i64>(Lc[m] + rec.X.Dy[m] * (i64)b);
-      }
+      int lo_i, hi_i;
+      bool ok;
       if (amb) {
         ++ctr.fallback;
-        ok = exact_row<STRICT, i64>(rec.X, nup, nlo, na, b, c, lo_i, hi_i);
-      } else if (ok) {
+        ok = exact_row_of_tet<STRICT>(p, t, b, c, lo_i, hi_i);
+      } else {
+        ok = lo <= hi;
         lo_i = (int)lo;
         hi_i = (int)hi;
       }
-    } else {
-      ok = exact_row<STRICT, i64>(rec.X, nup, nlo, na, b, c, lo_i, hi_i);
-    }
-    ++ctr.rows;
-    if (ok) or_span(row, rec.i0 + lo_i, rec.i0 + hi_i);
-    if (++b == nb) {
-      b = 0;
-      ++c;
-      if (r + 1 < r1) set_slice(c);
-      row = p.out + ((size_t)(rec.l0 + c) * p.res + rec.j0) * p.W;
-    } else {
-      row += p.W;
+      if (ok) or_span(row, bx.i0 + lo_i, bx.i0 + hi_i);
     }
   }
 }
 
 // ------------------------------------------------------------------ the fused kernel
 
-template <bool STRICT, bool FILTER>
-__global__ void __launch_bounds__(kBlock, 2) k_voxelize(Params p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  TetRec *recs = reinterpret_cast<TetRec *>(smem_raw);
-  __shared__ uint32_t off[kBlock + 1];
+constexpr int kTile = 1024;  // tets per tile
+constexpr int kPerThread = kTile / kBlock;
+
+template <bool STRICT, bool FILTER, bool YRANGE>
+__global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p) {
+  __shared__ uint32_t off[kTile + 1];
   __shared__ uint32_t warp_tot[kBlock / 32];
   __shared__ unsigned long long tile_s;
+  __shared__ uint32_t next_span;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int err = 0;
@@ -382,18 +432,26 @@ __global__ void __launch_bounds__(kBlock, 2) k_voxelize(Params p) {
   RowCounters ctr;
 
   for (;;) {
-    if (tid == 0) tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
+    if (tid == 0) {
+      tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
+      next_span = 0;
+    }
     __syncthreads();
-    const long long base = (long long)tile_s * kBlock;
+    const long long base = (long long)tile_s * kTile;
     if (base >= p.n_tets) break;
 
-    // (1) per-tet box, orientation, row count
-    const long long t = base + tid;
-    uint32_t cnt = 0;
-    if (t < p.n_tets) cnt = setup_tet<FILTER>(p, t, recs[tid], err, n_degenerate, n_wide);
+    // (1) box, orientation and span count of this thread's kPerThread consecutive tets
+    uint32_t cnt[kPerThread];
+    uint32_t mine = 0;
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+      const long long t = base + (long long)tid * kPerThread + k;
+      cnt[k] = t < p.n_tets ? count_spans(p, t, err, n_degenerate, n_wide) : 0u;
+      mine += cnt[k];
+    }
 
     // (2) block-wide exclusive prefix sum of span counts
-    uint32_t x = cnt;
+    uint32_t x = mine;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
@@ -408,35 +466,44 @@ __global__ void __launch_bounds__(kBlock, 2) k_voxelize(Params p) {
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, d);
         if (lane >= d) w += y;
       }
-      if (lane < kBlock / 32) warp_tot[lane] = w;  // inclusive warp prefix
+      if (lane < kBlock / 32) warp_tot[lane] = w;
     }
     __syncthreads();
-    const uint32_t warp_base = warp ? warp_tot[warp - 1] : 0u;
-    off[tid] = warp_base + x - cnt;
-    if (tid == kBlock - 1) off[kBlock] = warp_base + x;
+    uint32_t run = (warp ? warp_tot[warp - 1] : 0u) + x - mine;
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+      off[tid * kPerThread + k] = run;
+      run += cnt[k];
+    }
+    if (tid == kBlock - 1) off[kTile] = run;
     __syncthreads();
-    const uint32_t total = off[kBlock];
-    n_spans += tid == 0 ? total : 0;
+    const uint32_t total = off[kTile];
+    if (tid == 0) n_spans += total;
 
-    // (3)+(4) spans: largest slot u with off[u] <= s owns span s
-    for (uint32_t s = tid; s < total; s += kBlock) {
-      int a = 0, bnd = kBlock - 1;
+    // (3)+(4) spans, claimed dynamically; tet slot = largest u with off[u] <= span
+    for (;;) {
+      const uint32_t sp = atomicAdd(&next_span, 1u);
+      if (sp >= total) break;
+      int a = 0, bnd = kTile - 1;
       while (a < bnd) {
         const int mid = (a + bnd + 1) >> 1;
-        if (off[mid] <= s) a = mid;
+        if (off[mid] <= sp) a = mid;
         else bnd = mid - 1;
       }
-      const TetRec &rec = recs[a];
-      const uint32_t R = (uint32_t)rec.rows_per_span;
-      const uint32_t rows = (uint32_t)rec.nb * (uint32_t)rec.nc;
-      const uint32_t r0 = (s - off[a]) * R;
-      const uint32_t r1 = min(r0 + R, rows);
-      span_rows<STRICT, FILTER>(p, rec, r0, r1, ctr);
+      const long long t = base + a;
+      int3 V[4];
+      Box bx;
+      int dummy = 0;
+      load_tet(p, t, V, dummy);
+      tet_box(V, p.sh, p.res, bx);
+      const int S = slices_per_span(p, bx.nb);
+      const int c0 = (int)(sp - off[a]) * S;
+      const int c1 = min(c0 + S, bx.nc);
+      run_span<STRICT, FILTER, YRANGE>(p, t, c0, c1, ctr);
     }
     __syncthreads();
   }
 
-  // counters: one atomic per warp
   unsigned long long rows_w = ctr.rows, fb_w = ctr.fallback, deg_w = n_degenerate, wide_w = n_wide;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
@@ -461,9 +528,24 @@ __global__ void __launch_bounds__(kBlock, 2) k_voxelize(Params p) {
 static std::atomic<unsigned long long> g_launches{0};
 
 constexpr int kMaxDevices = 64;
+typedef void (*VoxKernel)(Params);
+// k_voxelize variants indexed by (strict << 2) | (filter << 1) | cull
+static VoxKernel voxelize_kernel(int idx) {
+  switch (idx) {
+    case 0: return k_voxelize<false, false, false>;
+    case 1: return k_voxelize<false, false, true>;
+    case 2: return k_voxelize<false, true, false>;
+    case 3: return k_voxelize<false, true, true>;
+    case 4: return k_voxelize<true, false, false>;
+    case 5: return k_voxelize<true, false, true>;
+    case 6: return k_voxelize<true, true, false>;
+    default: return k_voxelize<true, true, true>;
+  }
+}
+
 struct DeviceInfo {
   int sms = 0;
-  int occ[4] = {0, 0, 0, 0};  // blocks per SM of k_voxelize<STRICT, FILTER>
+  int occ[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // resident blocks per SM of each k_voxelize variant
   bool ready = false;
 };
 static DeviceInfo g_dev[kMaxDevices];
@@ -496,16 +578,6 @@ static cudaError_t profile_begin(cudaStream_t stream) {
   return cudaEventRecord(t_prof.start, stream);
 }
 
-static size_t rec_smem() { return (size_t)kBlock * sizeof(TetRec); }
-
-template <bool S, bool F>
-static cudaError_t prepare_kernel(int &occ) {
-  cudaError_t e = cudaFuncSetAttribute(k_voxelize<S, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)rec_smem());
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize<S, F>, kBlock, rec_smem());
-}
-
 static cudaError_t device_info(DeviceInfo *&out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -517,10 +589,8 @@ static cudaError_t device_info(DeviceInfo *&out) {
     }
     if (!d.ready) {
       e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
-      if (e == cudaSuccess) e = prepare_kernel<false, false>(d.occ[0]);
-      if (e == cudaSuccess) e = prepare_kernel<false, true>(d.occ[1]);
-      if (e == cudaSuccess) e = prepare_kernel<true, false>(d.occ[2]);
-      if (e == cudaSuccess) e = prepare_kernel<true, true>(d.occ[3]);
+      for (int v = 0; v < 8 && e == cudaSuccess; ++v)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[v], voxelize_kernel(v), kBlock, 0);
       if (e == cudaSuccess) d.ready = true;
     }
     g_dev_lock.store(0);
@@ -559,6 +629,7 @@ static int check_opts(const voxtet_opts &o) {
   if (o.span_rows < 0 || o.span_rows > (1 << 20)) return VOXTET_ERR_ARG;
   if (o.block != 0 && o.block != kBlock) return VOXTET_ERR_ARG;
   if (o.profile != 0 && o.profile != 1) return VOXTET_ERR_ARG;
+  if (o.row_cull < 0 || o.row_cull > 2) return VOXTET_ERR_ARG;
   return VOXTET_OK;
 }
 
@@ -579,18 +650,13 @@ static int run_voxelize(const int4 *verts4, long long n_verts, const int32_t *te
     p.W = (res + 31) / 32;
     p.sh = kLatticeBits - k;
     p.span_rows = o.span_rows > 0 ? o.span_rows : kDefaultSpanRows;
-    const long long tiles = (n_tets + kBlock - 1) / kBlock;
-    const int variant = (o.mode == 1 ? 2 : 0) + (o.use_filter ? 1 : 0);
+    const long long tiles = (n_tets + kTile - 1) / kTile;
+    const bool cull = o.row_cull == 1 || (o.row_cull == 0 && res >= kCullMinRes);
+    const int variant = (o.mode == 1 ? 4 : 0) | (o.use_filter ? 2 : 0) | (cull ? 1 : 0);
     long long grid = (long long)dev->sms * (dev->occ[variant] > 0 ? dev->occ[variant] : 1);
     if (grid > tiles) grid = tiles;
-    const size_t sm = rec_smem();
     if (o.profile && profile_begin(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
-    switch (variant) {
-      case 0: k_voxelize<false, false><<<(unsigned)grid, kBlock, sm, stream>>>(p); break;
-      case 1: k_voxelize<false, true><<<(unsigned)grid, kBlock, sm, stream>>>(p); break;
-      case 2: k_voxelize<true, false><<<(unsigned)grid, kBlock, sm, stream>>>(p); break;
-      default: k_voxelize<true, true><<<(unsigned)grid, kBlock, sm, stream>>>(p); break;
-    }
+    voxelize_kernel(variant)<<<(unsigned)grid, kBlock, 0, stream>>>(p);
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
     if (o.profile) {
@@ -658,6 +724,7 @@ void voxtet_default_opts(voxtet_opts *o) {
   o->span_rows = 0;
   o->block = 0;
   o->profile = 0;
+  o->row_cull = 0;
 }
 
 size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res) {

@@ -30,7 +30,7 @@ EXPORTED = (
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("accumulate", ctypes.c_int32), ("use_filter", ctypes.c_int32),
                 ("sync", ctypes.c_int32), ("span_rows", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("row_cull", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -101,11 +101,11 @@ def workspace_size(n_tets: int, n_verts: int, res: int) -> int:
 
 
 def make_opts(mode: int = 0, accumulate: bool = False, use_filter: bool = True, sync: bool = True,
-              span_rows: int = 0, block: int = 0, profile: bool = False) -> Opts:
+              span_rows: int = 0, block: int = 0, profile: bool = False, row_cull: int = 0) -> Opts:
     o = Opts()
     load().voxtet_default_opts(ctypes.byref(o))
     o.mode, o.accumulate, o.use_filter, o.sync = int(mode), int(bool(accumulate)), int(bool(use_filter)), int(bool(sync))
-    o.span_rows, o.block, o.profile = int(span_rows), int(block), int(bool(profile))
+    o.span_rows, o.block, o.profile, o.row_cull = int(span_rows), int(block), int(bool(profile)), int(row_cull)
     return o
 
 
@@ -145,7 +145,8 @@ def alloc_workspace(n_tets: int, n_verts: int, res: int, device=None):
 
 def voxelize(verts, tets, origin: Sequence[float], voxel_size: float, res: int, out=None, workspace=None,
              mode: int = 0, accumulate: bool = False, use_filter: bool = True, sync: bool = True,
-             span_rows: int = 0, stream=None, raise_on_error: bool = True, profile: bool = False):
+             span_rows: int = 0, stream=None, raise_on_error: bool = True, profile: bool = False,
+             row_cull: int = 0):
     """Grid (int32 tensor [res, res, W] of uint32 bit words) of a world-space mesh.
 
     verts: float32 CUDA [n_verts, 3]; tets: int32 CUDA [n_tets, 4].  Returns ``out``
@@ -161,7 +162,7 @@ def voxelize(verts, tets, origin: Sequence[float], voxel_size: float, res: int, 
     _check_cuda_tensor(out, "out", torch.int32)
     if workspace is None:
         workspace = alloc_workspace(n_t, n_v, res, verts.device)
-    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile)
+    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull)
     org = (ctypes.c_float * 3)(*[float(x) for x in origin])
     st = lib.voxelize_tets(verts.data_ptr(), n_v, tets.data_ptr(), n_t, ctypes.byref(org), float(voxel_size),
                            int(res), out.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(o),
@@ -175,7 +176,7 @@ def voxelize(verts, tets, origin: Sequence[float], voxel_size: float, res: int, 
 
 def voxelize_fixed(xyz, tets, res: int, out=None, workspace=None, mode: int = 0, accumulate: bool = False,
                    use_filter: bool = True, sync: bool = True, span_rows: int = 0, stream=None,
-                   raise_on_error: bool = True, profile: bool = False):
+                   raise_on_error: bool = True, profile: bool = False, row_cull: int = 0):
     """Grid of a mesh whose vertices are already on the 2^20-per-grid lattice (int32 [n, 3])."""
     torch = _torch()
     lib = load()
@@ -187,7 +188,7 @@ def voxelize_fixed(xyz, tets, res: int, out=None, workspace=None, mode: int = 0,
     _check_cuda_tensor(out, "out", torch.int32)
     if workspace is None:
         workspace = alloc_workspace(n_t, n_v, res, xyz.device)
-    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile)
+    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull)
     st = lib.voxelize_tets_fixed(xyz.data_ptr(), n_v, tets.data_ptr(), n_t, int(res), out.data_ptr(),
                                  workspace.data_ptr(), workspace.numel(), ctypes.byref(o), _stream_ptr(stream))
     if raise_on_error:
