@@ -81,21 +81,25 @@ typedef struct {
 /* Counters the last call on a workspace left in it (read with voxtet_read_stats). */
 typedef struct {
     uint64_t spans;           /* work items (tet, run of x-rows) distributed to threads */
-    uint64_t rows;            /* x-rows of tet bounding boxes visited */
-    uint64_t fallback_rows;   /* rows whose interval the filter could not certify (solved exactly) */
+    uint64_t rows;            /* x-rows solved by the single-precision filter */
+    uint64_t fallback_rows;   /* rows the filter could not certify (re-solved with exact integers) */
     uint64_t degenerate_tets; /* tetrahedra with zero signed volume (skipped) */
     uint64_t wide_tets;       /* tetrahedra wider than 2^20 lattice units (128-bit exact path) */
     uint64_t kernel_ns;       /* device time of the main kernel of the last profiled call on this thread, else 0 */
-    uint64_t reserved[2];
+    uint64_t exact_tets;      /* tetrahedra solved entirely with exact integers (wide, a face parallel to x,
+                                 or use_filter = 0) */
+    uint64_t reserved;
 } voxtet_stats;
 
 /* Fill *opts with the defaults listed above. */
 void voxtet_default_opts(voxtet_opts *opts);
 
-/* Bytes of device workspace a call with these sizes needs (>= 256; the
- * workspace must be 256-byte aligned).  It holds a 256-byte status/counter
- * header and the snapped vertices (16 B per vertex).  Returns 0 for negative
- * sizes. */
+/* Bytes of device workspace a call with these sizes needs (the workspace must
+ * be 256-byte aligned).  It holds a 256-byte status/counter header, the snapped
+ * vertices (16 B per vertex), a queue of tetrahedra for the exact solver (4 B per
+ * tetrahedron), a queue of rows the filter could not certify (8 B per entry,
+ * max(65536, n_tets / 4) entries) and a redo bitmap (1 bit per tetrahedron).
+ * Returns 0 for negative sizes. */
 size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res);
 
 /* Voxelize a mesh given in world coordinates (Section 3, "Voxelization";

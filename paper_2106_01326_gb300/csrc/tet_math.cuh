@@ -190,7 +190,7 @@ __device__ __forceinline__ bool lam_ok(T v) {
 // returns false if the row has no sample.  Each bound is found by bisection on the
 // monotone exact lam(a) = H + Dx a, probing only a in [0, na-1] (inside the box).
 template <bool STRICT, typename T>
-__device__ __noinline__ bool exact_row(const Exact<T> &X, int nup, int nlo, int na, int b, int c, int &lo_out,
+__device__ __forceinline__ bool exact_row(const Exact<T> &X, int nup, int nlo, int na, int b, int c, int &lo_out,
                                        int &hi_out) {
   int lo = 0, hi = na - 1;
 #pragma unroll 1

@@ -9,19 +9,28 @@
 // becomes a per-row interval.
 //
 // Kernels (one stream, in order):
-//   k_prologue   zero the workspace header and (unless accumulating) the grid
+//   k_prologue   zero the workspace header and redo bitmap, and (unless
+//                accumulating) the grid
 //   k_snap       float vertices -> lattice int4 (x, y, z, flag); k_load_fixed
 //                does the range check for vertices already on the lattice
 //   k_voxelize   persistent; each block repeatedly claims a tile of tets and
-//                (1) computes per tet the sample box, orientation and row count,
-//                    staging the exact and filter data in shared memory,
-//                (2) splits the tile into spans of at most R x-rows with a
-//                    block-wide exclusive prefix sum,
-//                (3) solves every row of every span for its sample interval
-//                    (filter + exact fallback), and
+//                (1) computes per tet the sample box, orientation and span
+//                    count (whole z-slices, about span_rows rows per span),
+//                (2) splits the tile into spans with a block-wide exclusive
+//                    prefix sum,
+//                (3) solves each row of each span for its sample interval with
+//                    the single-precision filter, skipping rows outside each
+//                    slice's cross-section, and
 //                (4) ORs the interval into the bit grid: whole 32-bit words are
 //                    stored, the two partial edge words use atomicOr since other
 //                    tets may share them.
+//                Work the filter cannot certify is queued, not solved here, so
+//                the hot loop carries no rarely used state: tets wider than 2^20
+//                lattice units or with a face parallel to x go to the tet queue,
+//                uncertain rows to the row queue (tets whose rows overflow it
+//                are flagged in the redo bitmap).
+//   k_exact      solves the queued tets and rows with exact integers and ORs
+//                them in (OR is idempotent, so redoing a row is harmless).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -44,16 +53,23 @@ constexpr int kCullMinRes = 256;        // automatic row culling from this resol
 // Workspace header (first 256 bytes of the workspace).
 struct Header {
   int status_bits;
-  int pad0;
+  unsigned tetq_count;  // tets queued for the exact kernel
+  unsigned rowq_count;  // rows queued for the exact kernel (may exceed the capacity)
+  unsigned pad0;
   unsigned long long tile_counter;
   unsigned long long spans;
   unsigned long long rows;
-  unsigned long long fallback_rows;
   unsigned long long degenerate;
   unsigned long long wide;
   unsigned long long reserved[25];
 };
 static_assert(sizeof(Header) == 256, "header is 256 bytes");
+
+// A row the filter could not certify: tet index and (b, c) within its sample box.
+struct RowItem {
+  uint32_t tet;
+  uint16_t b, c;
+};
 
 struct Params {
   const int4 *verts4;
@@ -62,18 +78,31 @@ struct Params {
   long long n_verts;
   uint32_t *out;
   Header *hdr;
+  uint32_t *tetq;   // [n_tets]
+  RowItem *rowq;    // [q_cap]
+  uint32_t *redo;   // [ceil(n_tets / 32)] bitmap
+  unsigned q_cap;
   int res;
   int W;
-  int sh;          // 20 - log2(res)
-  int span_rows;   // target bounding-box rows per span
+  int sh;           // 20 - log2(res)
+  int span_rows;    // target bounding-box rows per span
+  int exact_all;    // 1: every tet goes to the exact kernel
 };
+
+// Row-queue capacity for a mesh of n_tets tets.
+static unsigned long long row_queue_capacity(long long n_tets) {
+  const long long q = n_tets / 4;
+  return (unsigned long long)(q < 65536 ? 65536 : q);
+}
 
 // ------------------------------------------------------------------ small kernels
 
-__global__ void k_prologue(Header *hdr, uint32_t *out, long long n_words, int clear) {
+__global__ void k_prologue(Header *hdr, uint32_t *redo, long long redo_words, uint32_t *out, long long n_words,
+                           int clear) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   if (tid < 64) reinterpret_cast<uint32_t *>(hdr)[tid] = 0u;
+  for (long long i = tid; i < redo_words; i += stride) redo[i] = 0u;
   if (!clear) return;
   if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {
     uint4 *o4 = reinterpret_cast<uint4 *>(out);
@@ -173,30 +202,7 @@ __device__ __forceinline__ bool load_tet(const Params &p, long long t, int3 V[4]
   return (A.w | B.w | C.w | D.w) == 0;
 }
 
-// z-slices per span: about span_rows bounding-box rows per work item.
-__device__ __forceinline__ int slices_per_span(const Params &p, int nb) {
-  const int S = p.span_rows / nb;
-  return S < 1 ? 1 : S;
-}
-
-// Phase (1): sample box, orientation and span count of tet t (0 if it marks nothing).
-__device__ uint32_t count_spans(const Params &p, long long t, int &err, unsigned &n_degenerate,
-                                unsigned &n_wide) {
-  int3 V[4];
-  if (!load_tet(p, t, V, err)) return 0;
-  Box bx;
-  const int E = tet_box(V, p.sh, p.res, bx);
-  if (v6_sign(V, E) == 0) {
-    ++n_degenerate;
-    return 0;
-  }
-  if (bx.na <= 0 || bx.nb <= 0 || bx.nc <= 0) return 0;
-  if (E > kNarrowExtent) ++n_wide;
-  const int S = slices_per_span(p, bx.nb);
-  return (uint32_t)((bx.nc + S - 1) / S);
-}
-
-// Loads, orients (V6 > 0) and boxes a tet already known to be live.
+// Loads, orients (V6 > 0) and boxes a tet already known to be live; returns its extent.
 __device__ __forceinline__ int oriented_tet(const Params &p, long long t, int3 V[4], Box &bx) {
   int dummy = 0;
   load_tet(p, t, V, dummy);
@@ -209,51 +215,56 @@ __device__ __forceinline__ int oriented_tet(const Params &p, long long t, int3 V
   return E;
 }
 
-struct RowCounters {
-  unsigned rows = 0, fallback = 0;
-};
-
-// Exact interval of row (b, c) of tet t, recomputed from scratch (the filter's rare
-// uncertain rows; 64-bit exact arithmetic, the tet is narrow).
-template <bool STRICT>
-__device__ __noinline__ bool exact_row_of_tet(const Params &p, long long t, int b, int c, int &lo, int &hi) {
-  int3 V[4];
-  Box bx;
-  oriented_tet(p, t, V, bx);
-  Exact<i64> X;
-  exact_setup<i64>(V, bx, p.sh, X);
-  int slot[4], nup = 0, nlo = 0;
-  slot_order<i64>(X, slot, nup, nlo);
-  permute_slots<i64>(X, slot);
-  return exact_row<STRICT, i64>(X, nup, nlo, bx.na, b, c, lo, hi);
+// True if some face has a normal with zero x component (its constraint does not
+// depend on the sample's x).  Requires E <= 2^20 (64-bit exact).
+__device__ __forceinline__ bool has_face_parallel_to_x(const int3 V[4]) {
+  const i64 e1y = V[1].y - V[0].y, e1z = V[1].z - V[0].z;
+  const i64 e2y = V[2].y - V[0].y, e2z = V[2].z - V[0].z;
+  const i64 e3y = V[3].y - V[0].y, e3z = V[3].z - V[0].z;
+  const i64 n1x = e2y * e3z - e2z * e3y;
+  const i64 n2x = e3y * e1z - e3z * e1y;
+  const i64 n3x = e1y * e2z - e1z * e2y;
+  const i64 n0x = -(n1x + n2x + n3x);
+  return n1x == 0 || n2x == 0 || n3x == 0 || n0x == 0;
 }
 
-// Tets wider than 2^20 lattice units, and the exact-only mode: every bounding-box row
-// of slices [c0, c1) solved with exact integers of type T.
-template <bool STRICT, typename T>
-__device__ __noinline__ void span_exact(const Params &p, long long t, int c0, int c1, RowCounters &ctr) {
+// z-slices per span: about span_rows bounding-box rows per work item, at most
+// kMaxSlicesPerSpan (the size of each thread's slice table).
+__device__ __forceinline__ int slices_per_span(const Params &p, int nb) {
+  const int S = p.span_rows / nb;
+  return S < 1 ? 1 : (S > 16 ? 16 : S);
+}
+
+// Phase (1): classify tet t and return its span count for the filter path (0 if it
+// marks nothing or was queued for the exact kernel).
+__device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, int &err, unsigned &n_degenerate,
+                                                 unsigned &n_wide) {
   int3 V[4];
+  if (!load_tet(p, t, V, err)) return 0;
   Box bx;
-  oriented_tet(p, t, V, bx);
-  Exact<T> X;
-  exact_setup<T>(V, bx, p.sh, X);
-  int slot[4], nup = 0, nlo = 0;
-  slot_order<T>(X, slot, nup, nlo);
-  permute_slots<T>(X, slot);
-  for (int c = c0; c < c1; ++c) {
-    uint32_t *row = p.out + ((size_t)(bx.l0 + c) * p.res + bx.j0) * p.W;
-    for (int b = 0; b < bx.nb; ++b, row += p.W) {
-      int lo, hi;
-      ++ctr.rows;
-      if (exact_row<STRICT, T>(X, nup, nlo, bx.na, b, c, lo, hi)) or_span(row, bx.i0 + lo, bx.i0 + hi);
-    }
+  const int E = tet_box(V, p.sh, p.res, bx);
+  if (v6_sign(V, E) == 0) {
+    ++n_degenerate;
+    return 0;
   }
+  if (bx.na <= 0 || bx.nb <= 0 || bx.nc <= 0) return 0;
+  const bool wide = E > kNarrowExtent;
+  n_wide += wide;
+  if (wide || p.exact_all || has_face_parallel_to_x(V)) {
+    const unsigned k = atomicAdd(&p.hdr->tetq_count, 1u);  // each tet is queued once: k < n_tets
+    p.tetq[k] = (uint32_t)t;
+    return 0;
+  }
+  const int S = slices_per_span(p, bx.nb);
+  return (uint32_t)((bx.nc + S - 1) / S);
 }
 
-// Rows of slice c that can hold samples: the y-extent of the tet's cross-section at
-// the slice's z, from the crossing points of its 6 edges, widened by 2 lattice units
-// (the float error of each crossing point is below 0.7 units: |t - t~| <= 2.01u and
-// |y| < 2^22), so the range is a superset of the non-empty rows.
+// Rows of slice Z that can hold samples: the y-extent of the tet's cross-section at
+// that z, from the crossing points of its 6 edges, widened by 2 lattice units (each
+// crossing point's float error is below 0.7 units: the edge parameter carries at
+// most two roundings, |dy| < 2^22 and |y| < 2^21), so the range is a superset of
+// the non-empty rows.  rz[e] = 1 / (z_q - z_p) of edge e (0 for horizontal edges,
+// which are skipped: their end points are covered by the other edges).
 __device__ __forceinline__ void slice_rows(const int3 V[4], const float rz[6], int Z, int s, int sh, int j0, int nb,
                                            int &b_lo, int &b_hi) {
   float ymin = 3.0e38f, ymax = -3.0e38f;
@@ -262,98 +273,74 @@ __device__ __forceinline__ void slice_rows(const int3 V[4], const float rz[6], i
     const int pi = e < 3 ? 0 : (e < 5 ? 1 : 2);
     const int qi = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
     const int zp = V[pi].z, zq = V[qi].z;
-    const bool cross = zp != zq && min(zp, zq) <= Z && Z <= max(zp, zq);
-    if (cross) {
+    if (zp != zq && min(zp, zq) <= Z && Z <= max(zp, zq)) {
       const float tpar = (float)(Z - zp) * rz[e];
       const float y = __fmaf_rn(tpar, (float)(V[qi].y - V[pi].y), (float)V[pi].y);
       ymin = fminf(ymin, y);
       ymax = fmaxf(ymax, y);
     }
   }
-  if (ymin > ymax) {  // cannot happen for a slice inside the box; be safe
+  if (ymin > ymax) {  // cannot happen for a slice inside the box; stay conservative
     b_lo = 0;
     b_hi = nb - 1;
     return;
   }
   const int ylo = (int)floorf(ymin) - 2, yhi = (int)ceilf(ymax) + 2;
-  const int jlo = (ylo + s - 1) >> sh, jhi = (yhi - s) >> sh;
-  b_lo = max(jlo - j0, 0);
-  b_hi = min(jhi - j0, nb - 1);
+  b_lo = max(((ylo + s - 1) >> sh) - j0, 0);
+  b_hi = min(((yhi - s) >> sh) - j0, nb - 1);
 }
 
-// Rows allowed by a constraint with Dx == 0 (lam = H0 + Dy b for the slice), exact:
-// narrows [b_lo, b_hi] by bisection on the monotone lam(b).
-template <bool STRICT>
-__device__ __forceinline__ void narrow_by_row_constraint(i64 H0, i64 Dy, int &b_lo, int &b_hi) {
-  if (b_lo > b_hi) return;
-  if (Dy == 0) {
-    if (!lam_ok<STRICT, i64>(H0)) b_hi = b_lo - 1;
-    return;
-  }
-  if (Dy > 0) {  // increasing: smallest b in [b_lo, b_hi + 1] that is ok
-    int x = b_lo, y = b_hi + 1;
-    while (x < y) {
-      const int mid = (x + y) >> 1;
-      if (lam_ok<STRICT, i64>(H0 + Dy * (i64)mid)) y = mid;
-      else x = mid + 1;
-    }
-    b_lo = x;
-  } else {  // decreasing: largest b in [b_lo - 1, b_hi] that is ok
-    int x = b_lo - 1, y = b_hi;
-    while (x < y) {
-      const int mid = (x + y + 1) >> 1;
-      if (lam_ok<STRICT, i64>(H0 + Dy * (i64)mid)) x = mid;
-      else y = mid - 1;
-    }
-    b_hi = x;
+// Queue row (b, c) of tet t for the exact kernel; if the row queue is full, flag the
+// whole tet for an exact redo instead.
+__device__ __forceinline__ void queue_row(const Params &p, long long t, int b, int c) {
+  const unsigned k = atomicAdd(&p.hdr->rowq_count, 1u);
+  if (k < p.q_cap) {
+    RowItem it;
+    it.tet = (uint32_t)t;
+    it.b = (uint16_t)b;
+    it.c = (uint16_t)c;
+    p.rowq[k] = it;
+  } else {
+    atomicOr(&p.redo[t >> 5], 1u << (t & 31));
   }
 }
 
-// Rows of slice c allowed by the (at most two) faces parallel to the x axis, whose
-// constraints do not depend on a.  Rare in general meshes, so the exact data is
-// recomputed here rather than kept live across the row loop.
-template <bool STRICT>
-__device__ __noinline__ void narrow_by_faces_parallel_to_x(const int3 V[4], const Box &bx, int sh, int c, int &b_lo,
-                                                           int &b_hi) {
-  Exact<i64> X;
-  exact_setup<i64>(V, bx, sh, X);
-#pragma unroll
-  for (int m = 0; m < 4; ++m)
-    if (X.Dx[m] == 0) narrow_by_row_constraint<STRICT>(X.L[m] + X.Dz[m] * (i64)c, X.Dy[m], b_lo, b_hi);
+// Exact conversion of an integral float in [0, 2^22) to int without the conversion
+// unit: adding 2^23 puts the integer in the low mantissa bits.
+__device__ __forceinline__ int small_float_to_int(float f) {
+  return __float_as_int(__fadd_rn(f, 8388608.0f)) - 0x4B000000;
 }
 
-// Phase (3)+(4): slices [c0, c1) of tet t.
-template <bool STRICT, bool FILTER, bool YRANGE>
-__device__ __forceinline__ void run_span(const Params &p, long long t, int c0, int c1, RowCounters &ctr) {
+constexpr int kMaxSlicesPerSpan = 16;
+
+// Phases (3)+(4): slices [c0, c1) (at most kMaxSlicesPerSpan) of a narrow tet whose
+// four faces all depend on x.  First the candidate rows of every slice are found and
+// written to this thread's column of `tab` (b_lo | count << 16), then one flat loop
+// walks all candidate rows, so the lanes of a warp stay in step across slices.
+// Returns the rows visited.
+template <bool STRICT, bool CULL>
+__device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c0, int c1,
+                                             uint32_t (*tab)[kBlock]) {
   int3 V[4];
   Box bx;
-  const int E = oriented_tet(p, t, V, bx);
-  if (E > kNarrowExtent) {
-    span_exact<STRICT, i128>(p, t, c0, c1, ctr);
-    return;
-  }
-  if (!FILTER) {
-    span_exact<STRICT, i64>(p, t, c0, c1, ctr);
-    return;
-  }
+  oriented_tet(p, t, V, bx);
   float al[4], be[4], ga[4], de[4];
-  unsigned fmask = 0, umask = 0;
+  unsigned umask = 0;
   {
     Exact<i64> X;
     exact_setup<i64>(V, bx, p.sh, X);
     const float fb = (float)(bx.nb - 1), fc = (float)(bx.nc - 1);
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
-      al[m] = be[m] = ga[m] = de[m] = 0.f;
-      if (X.Dx[m] != 0) {
-        fmask |= 1u << m;
-        if (X.Dx[m] < 0) umask |= 1u << m;
-        filter_slot(X.L[m], X.Dx[m], X.Dy[m], X.Dz[m], fb, fc, al[m], be[m], ga[m], de[m]);
-      }
+      umask |= (X.Dx[m] < 0 ? 1u : 0u) << m;
+      filter_slot(X.L[m], X.Dx[m], X.Dy[m], X.Dz[m], fb, fc, al[m], be[m], ga[m], de[m]);
     }
   }
-  float rz[6];
-  if (YRANGE) {
+  const int tid = threadIdx.x;
+  const int ns = c1 - c0;
+  unsigned total = 0;
+  if (CULL) {
+    float rz[6];
 #pragma unroll
     for (int e = 0; e < 6; ++e) {
       const int pi = e < 3 ? 0 : (e < 5 ? 1 : 2);
@@ -361,56 +348,67 @@ __device__ __forceinline__ void run_span(const Params &p, long long t, int c0, i
       const int dz = V[qi].z - V[pi].z;
       rz[e] = dz != 0 ? __frcp_rn((float)dz) : 0.f;
     }
-  }
-  const int s = 1 << (p.sh - 1);
-  const float fhi0 = (float)(bx.na - 1);
-  for (int c = c0; c < c1; ++c) {
-    int b_lo = 0, b_hi = bx.nb - 1;
-    if (YRANGE) slice_rows(V, rz, s + ((bx.l0 + c) << p.sh), s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
-    if (fmask != 0xFu) narrow_by_faces_parallel_to_x<STRICT>(V, bx, p.sh, c, b_lo, b_hi);
-    const float cf = (float)c;
-    float ac[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) ac[m] = __fmaf_rn(ga[m], cf, al[m]);
-    uint32_t *row = p.out + ((size_t)(bx.l0 + c) * p.res + (bx.j0 + b_lo)) * p.W;
-    for (int b = b_lo; b <= b_hi; ++b, row += p.W) {
-      ++ctr.rows;
-      const float bf = (float)b;
-      float lo = 0.f, hi = fhi0;
-      bool amb = false;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        if ((fmask >> m) & 1u) {
-          const float tt = __fmaf_rn(be[m], bf, ac[m]);
-          const float tl = __fsub_rd(tt, de[m]);
-          const float th = __fadd_ru(tt, de[m]);
-          float v;
-          if (STRICT) {
-            const float cc = ceilf(tl);
-            amb |= cc < th;
-            v = cc - 1.f;
-          } else {
-            const float f = floorf(th);
-            amb |= f > tl;
-            v = f;
-          }
-          if ((umask >> m) & 1u) hi = fminf(hi, v);
-          else lo = fmaxf(lo, -v);
-        }
-      }
-      int lo_i, hi_i;
-      bool ok;
-      if (amb) {
-        ++ctr.fallback;
-        ok = exact_row_of_tet<STRICT>(p, t, b, c, lo_i, hi_i);
-      } else {
-        ok = lo <= hi;
-        lo_i = (int)lo;
-        hi_i = (int)hi;
-      }
-      if (ok) or_span(row, bx.i0 + lo_i, bx.i0 + hi_i);
+    const int s = 1 << (p.sh - 1);
+    for (int k = 0; k < ns; ++k) {
+      int b_lo, b_hi;
+      slice_rows(V, rz, s + ((bx.l0 + c0 + k) << p.sh), s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
+      const int n = b_hi >= b_lo ? b_hi - b_lo + 1 : 0;
+      tab[k][tid] = (uint32_t)b_lo | ((uint32_t)n << 16);
+      total += (unsigned)n;
     }
+  } else {
+    for (int k = 0; k < ns; ++k) tab[k][tid] = (uint32_t)bx.nb << 16;
+    total = (unsigned)(ns * bx.nb);
   }
+  if (total == 0) return 0;
+
+  // walk the candidate rows slice by slice
+  int k = -1, b = 0, b_end = 0;
+  float bf = 0.f, ac[4];
+  uint32_t *row = p.out;
+  const float fhi0 = (float)(bx.na - 1);
+  for (unsigned r = 0; r < total; ++r) {
+    if (b == b_end) {  // next non-empty slice
+      uint32_t e;
+      do {
+        ++k;
+        e = tab[k][tid];
+      } while ((e >> 16) == 0u);
+      b = (int)(e & 0xFFFFu);
+      b_end = b + (int)(e >> 16);
+      bf = (float)b;
+      const float cf = (float)(c0 + k);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) ac[m] = __fmaf_rn(ga[m], cf, al[m]);
+      row = p.out + ((size_t)(bx.l0 + c0 + k) * p.res + (bx.j0 + b)) * p.W;
+    }
+    float lo = 0.f, hi = fhi0;
+    bool amb = false;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const float tt = __fmaf_rn(be[m], bf, ac[m]);
+      const float tl = __fsub_rd(tt, de[m]);
+      const float th = __fadd_ru(tt, de[m]);
+      float v;
+      if (STRICT) {
+        const float cc = ceilf(tl);
+        amb |= cc < th;
+        v = cc - 1.f;
+      } else {
+        const float f = floorf(th);
+        amb |= f > tl;
+        v = f;
+      }
+      if ((umask >> m) & 1u) hi = fminf(hi, v);
+      else lo = fmaxf(lo, -v);
+    }
+    if (amb) queue_row(p, t, b, c0 + k);
+    else if (lo <= hi) or_span(row, bx.i0 + small_float_to_int(lo), bx.i0 + small_float_to_int(hi));
+    ++b;
+    bf += 1.f;
+    row += p.W;
+  }
+  return total;
 }
 
 // ------------------------------------------------------------------ the fused kernel
@@ -418,35 +416,31 @@ __device__ __forceinline__ void run_span(const Params &p, long long t, int c0, i
 constexpr int kTile = 1024;  // tets per tile
 constexpr int kPerThread = kTile / kBlock;
 
-template <bool STRICT, bool FILTER, bool YRANGE>
+template <bool STRICT, bool CULL>
 __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p) {
   __shared__ uint32_t off[kTile + 1];
   __shared__ uint32_t warp_tot[kBlock / 32];
+  __shared__ uint32_t slice_tab[kMaxSlicesPerSpan][kBlock];
   __shared__ unsigned long long tile_s;
-  __shared__ uint32_t next_span;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   int err = 0;
-  unsigned n_degenerate = 0, n_wide = 0;
+  unsigned n_degenerate = 0, n_wide = 0, n_rows = 0;
   unsigned long long n_spans = 0;
-  RowCounters ctr;
 
   for (;;) {
-    if (tid == 0) {
-      tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
-      next_span = 0;
-    }
+    if (tid == 0) tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
     __syncthreads();
     const long long base = (long long)tile_s * kTile;
     if (base >= p.n_tets) break;
 
-    // (1) box, orientation and span count of this thread's kPerThread consecutive tets
+    // (1) classification and span counts of this thread's kPerThread consecutive tets
     uint32_t cnt[kPerThread];
     uint32_t mine = 0;
 #pragma unroll
     for (int k = 0; k < kPerThread; ++k) {
       const long long t = base + (long long)tid * kPerThread + k;
-      cnt[k] = t < p.n_tets ? count_spans(p, t, err, n_degenerate, n_wide) : 0u;
+      cnt[k] = t < p.n_tets ? classify_tet(p, t, err, n_degenerate, n_wide) : 0u;
       mine += cnt[k];
     }
 
@@ -480,10 +474,9 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
     const uint32_t total = off[kTile];
     if (tid == 0) n_spans += total;
 
-    // (3)+(4) spans, claimed dynamically; tet slot = largest u with off[u] <= span
-    for (;;) {
-      const uint32_t sp = atomicAdd(&next_span, 1u);
-      if (sp >= total) break;
+    // (3)+(4) spans in order, so the lanes of a warp start on neighbouring tets;
+    // the tet slot of span sp is the largest u with off[u] <= sp
+    for (uint32_t sp = tid; sp < total; sp += kBlock) {
       int a = 0, bnd = kTile - 1;
       while (a < bnd) {
         const int mid = (a + bnd + 1) >> 1;
@@ -498,24 +491,21 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
       tet_box(V, p.sh, p.res, bx);
       const int S = slices_per_span(p, bx.nb);
       const int c0 = (int)(sp - off[a]) * S;
-      const int c1 = min(c0 + S, bx.nc);
-      run_span<STRICT, FILTER, YRANGE>(p, t, c0, c1, ctr);
+      n_rows += run_span<STRICT, CULL>(p, t, c0, min(c0 + S, bx.nc), slice_tab);
     }
     __syncthreads();
   }
 
-  unsigned long long rows_w = ctr.rows, fb_w = ctr.fallback, deg_w = n_degenerate, wide_w = n_wide;
+  unsigned long long rows_w = n_rows, deg_w = n_degenerate, wide_w = n_wide;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     rows_w += __shfl_down_sync(0xFFFFFFFFu, rows_w, d);
-    fb_w += __shfl_down_sync(0xFFFFFFFFu, fb_w, d);
     deg_w += __shfl_down_sync(0xFFFFFFFFu, deg_w, d);
     wide_w += __shfl_down_sync(0xFFFFFFFFu, wide_w, d);
   }
   err = __reduce_or_sync(0xFFFFFFFFu, err);
   if (lane == 0) {
     if (rows_w) atomicAdd(&p.hdr->rows, rows_w);
-    if (fb_w) atomicAdd(&p.hdr->fallback_rows, fb_w);
     if (deg_w) atomicAdd(&p.hdr->degenerate, deg_w);
     if (wide_w) atomicAdd(&p.hdr->wide, wide_w);
     if (err) atomicOr(&p.hdr->status_bits, err);
@@ -523,29 +513,89 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
   if (tid == 0 && n_spans) atomicAdd(&p.hdr->spans, n_spans);
 }
 
+// ------------------------------------------------------------------ the exact kernel
+
+// Every bounding-box row of tet t, solved with exact integers of type T by the
+// threads of one block (threads stride over the rows).
+template <bool STRICT, typename T>
+__device__ __forceinline__ void exact_tet_rows(const Params &p, const int3 V[4], const Box &bx) {
+  Exact<T> X;
+  exact_setup<T>(V, bx, p.sh, X);
+  int slot[4], nup = 0, nlo = 0;
+  slot_order<T>(X, slot, nup, nlo);
+  permute_slots<T>(X, slot);
+  const unsigned rows = (unsigned)bx.nb * (unsigned)bx.nc;
+  for (unsigned r = threadIdx.x; r < rows; r += blockDim.x) {
+    const int c = (int)(r / (unsigned)bx.nb), b = (int)(r - (unsigned)c * bx.nb);
+    int lo, hi;
+    if (exact_row<STRICT, T>(X, nup, nlo, bx.na, b, c, lo, hi)) {
+      uint32_t *row = p.out + ((size_t)(bx.l0 + c) * p.res + (bx.j0 + b)) * p.W;
+      or_span(row, bx.i0 + lo, bx.i0 + hi);
+    }
+  }
+}
+
+template <bool STRICT>
+__device__ __forceinline__ void exact_tet(const Params &p, long long t) {
+  int3 V[4];
+  Box bx;
+  const int E = oriented_tet(p, t, V, bx);
+  if (E <= kNarrowExtent) exact_tet_rows<STRICT, i64>(p, V, bx);
+  else exact_tet_rows<STRICT, i128>(p, V, bx);
+}
+
+template <bool STRICT>
+__global__ void __launch_bounds__(128) k_exact(Params p) {
+  const unsigned n_tq = min((unsigned long long)p.hdr->tetq_count, (unsigned long long)p.n_tets);
+  const unsigned n_rq_all = p.hdr->rowq_count;
+  const unsigned n_rq = min(n_rq_all, p.q_cap);
+  // queued tets: one block each
+  for (unsigned q = blockIdx.x; q < n_tq; q += gridDim.x) exact_tet<STRICT>(p, p.tetq[q]);
+  // queued rows: one thread each (these tets are narrow: 64-bit exact)
+  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  for (unsigned i = gtid; i < n_rq; i += gsz) {
+    const RowItem it = p.rowq[i];
+    int3 V[4];
+    Box bx;
+    oriented_tet(p, it.tet, V, bx);
+    Exact<i64> X;
+    exact_setup<i64>(V, bx, p.sh, X);
+    int slot[4], nup = 0, nlo = 0;
+    slot_order<i64>(X, slot, nup, nlo);
+    permute_slots<i64>(X, slot);
+    int lo, hi;
+    if (exact_row<STRICT, i64>(X, nup, nlo, bx.na, it.b, it.c, lo, hi)) {
+      uint32_t *row = p.out + ((size_t)(bx.l0 + it.c) * p.res + (bx.j0 + it.b)) * p.W;
+      or_span(row, bx.i0 + lo, bx.i0 + hi);
+    }
+  }
+  // row-queue overflow: whole tets flagged in the redo bitmap
+  if (n_rq_all > p.q_cap) {
+    for (long long t = blockIdx.x; t < p.n_tets; t += gridDim.x)
+      if ((p.redo[t >> 5] >> (t & 31)) & 1u) exact_tet<STRICT>(p, t);
+  }
+}
+
 // ------------------------------------------------------------------ host side
 
 static std::atomic<unsigned long long> g_launches{0};
 
 constexpr int kMaxDevices = 64;
+constexpr int kExactBlock = 128;
 typedef void (*VoxKernel)(Params);
-// k_voxelize variants indexed by (strict << 2) | (filter << 1) | cull
+// k_voxelize variants indexed by (strict << 1) | cull
 static VoxKernel voxelize_kernel(int idx) {
   switch (idx) {
-    case 0: return k_voxelize<false, false, false>;
-    case 1: return k_voxelize<false, false, true>;
-    case 2: return k_voxelize<false, true, false>;
-    case 3: return k_voxelize<false, true, true>;
-    case 4: return k_voxelize<true, false, false>;
-    case 5: return k_voxelize<true, false, true>;
-    case 6: return k_voxelize<true, true, false>;
-    default: return k_voxelize<true, true, true>;
+    case 0: return k_voxelize<false, false>;
+    case 1: return k_voxelize<false, true>;
+    case 2: return k_voxelize<true, false>;
+    default: return k_voxelize<true, true>;
   }
 }
 
 struct DeviceInfo {
   int sms = 0;
-  int occ[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // resident blocks per SM of each k_voxelize variant
+  int occ[4] = {0, 0, 0, 0};  // resident blocks per SM of each k_voxelize variant
   bool ready = false;
 };
 static DeviceInfo g_dev[kMaxDevices];
@@ -589,7 +639,7 @@ static cudaError_t device_info(DeviceInfo *&out) {
     }
     if (!d.ready) {
       e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
-      for (int v = 0; v < 8 && e == cudaSuccess; ++v)
+      for (int v = 0; v < 4 && e == cudaSuccess; ++v)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[v], voxelize_kernel(v), kBlock, 0);
       if (e == cudaSuccess) d.ready = true;
     }
@@ -608,6 +658,42 @@ static int log2_res(int res) {
 }
 
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Carved workspace: header, snapped vertices, tet queue, row queue, redo bitmap.
+struct Workspace {
+  Header *hdr;
+  int4 *verts4;
+  uint32_t *tetq;
+  RowItem *rowq;
+  uint32_t *redo;
+  unsigned q_cap;
+  long long redo_words;
+};
+
+static size_t workspace_bytes(long long n_tets, long long n_verts, Workspace *w, void *base) {
+  const unsigned long long q = row_queue_capacity(n_tets);
+  const long long redo_words = (n_tets + 31) / 32;
+  size_t o = sizeof(Header);
+  const size_t o_v = o;
+  o += align256((size_t)n_verts * sizeof(int4));
+  const size_t o_t = o;
+  o += align256((size_t)n_tets * sizeof(uint32_t));
+  const size_t o_r = o;
+  o += align256((size_t)q * sizeof(RowItem));
+  const size_t o_b = o;
+  o += align256((size_t)redo_words * sizeof(uint32_t));
+  if (w) {
+    char *c = reinterpret_cast<char *>(base);
+    w->hdr = reinterpret_cast<Header *>(c);
+    w->verts4 = reinterpret_cast<int4 *>(c + o_v);
+    w->tetq = reinterpret_cast<uint32_t *>(c + o_t);
+    w->rowq = reinterpret_cast<RowItem *>(c + o_r);
+    w->redo = reinterpret_cast<uint32_t *>(c + o_b);
+    w->q_cap = (unsigned)q;
+    w->redo_words = redo_words;
+  }
+  return o;
+}
 
 static int map_status_bits(int bits) {
   if (bits & kErrNan) return VOXTET_ERR_NAN;
@@ -634,25 +720,30 @@ static int check_opts(const voxtet_opts &o) {
 }
 
 // Shared tail of both entry points: vertices are already in the workspace.
-static int run_voxelize(const int4 *verts4, long long n_verts, const int32_t *tets, long long n_tets, int res,
-                        int k, uint32_t *out, Header *hdr, const voxtet_opts &o, cudaStream_t stream) {
+static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *tets, long long n_tets, int res, int k,
+                        uint32_t *out, const voxtet_opts &o, cudaStream_t stream) {
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   if (n_tets > 0) {
     Params p;
-    p.verts4 = verts4;
+    p.verts4 = w.verts4;
     p.tets = reinterpret_cast<const int4 *>(tets);
     p.n_tets = n_tets;
     p.n_verts = n_verts;
     p.out = out;
-    p.hdr = hdr;
+    p.hdr = w.hdr;
+    p.tetq = w.tetq;
+    p.rowq = w.rowq;
+    p.redo = w.redo;
+    p.q_cap = w.q_cap;
     p.res = res;
     p.W = (res + 31) / 32;
     p.sh = kLatticeBits - k;
     p.span_rows = o.span_rows > 0 ? o.span_rows : kDefaultSpanRows;
+    p.exact_all = o.use_filter ? 0 : 1;
     const long long tiles = (n_tets + kTile - 1) / kTile;
     const bool cull = o.row_cull == 1 || (o.row_cull == 0 && res >= kCullMinRes);
-    const int variant = (o.mode == 1 ? 4 : 0) | (o.use_filter ? 2 : 0) | (cull ? 1 : 0);
+    const int variant = (o.mode == 1 ? 2 : 0) | (cull ? 1 : 0);
     long long grid = (long long)dev->sms * (dev->occ[variant] > 0 ? dev->occ[variant] : 1);
     if (grid > tiles) grid = tiles;
     if (o.profile && profile_begin(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
@@ -663,25 +754,30 @@ static int run_voxelize(const int4 *verts4, long long n_verts, const int32_t *te
       if (cudaEventRecord(t_prof.stop, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
       t_prof.pending = true;
     }
+    const unsigned eg = (unsigned)dev->sms * 4;
+    if (o.mode == 1) k_exact<true><<<eg, kExactBlock, 0, stream>>>(p);
+    else k_exact<false><<<eg, kExactBlock, 0, stream>>>(p);
+    g_launches.fetch_add(1);
+    if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
   }
   if (o.sync) {
     if (cudaStreamSynchronize(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
     int bits = 0;
-    if (cudaMemcpy(&bits, &hdr->status_bits, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (cudaMemcpy(&bits, &w.hdr->status_bits, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
       return VOXTET_ERR_CUDA;
     return map_status_bits(bits);
   }
   return VOXTET_OK;
 }
 
-static int launch_prologue(Header *hdr, uint32_t *out, long long n_words, int clear, cudaStream_t stream) {
+static int launch_prologue(const Workspace &w, uint32_t *out, long long n_words, int clear, cudaStream_t stream) {
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
-  long long blocks = clear ? (n_words / 4 + 255) / 256 : 1;
+  long long blocks = clear ? (n_words / 4 + 255) / 256 : (w.redo_words + 255) / 256;
   const long long cap = (long long)dev->sms * 8;
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
-  k_prologue<<<(unsigned)blocks, 256, 0, stream>>>(hdr, out, n_words, clear);
+  k_prologue<<<(unsigned)blocks, 256, 0, stream>>>(w.hdr, w.redo, w.redo_words, out, n_words, clear);
   g_launches.fetch_add(1);
   return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
 }
@@ -699,7 +795,7 @@ static int common_checks(long long n_verts, const void *tets, long long n_tets, 
   if (st != VOXTET_OK) return st;
   k = log2_res(res);
   if (k < 0) return VOXTET_ERR_RES;
-  if (n_verts < 0 || n_tets < 0 || n_verts > 0x7FFFFFFFLL) return VOXTET_ERR_ARG;
+  if (n_verts < 0 || n_tets < 0 || n_verts > 0x7FFFFFFFLL || n_tets > 0xFFFFFFFFLL) return VOXTET_ERR_ARG;
   if (!out) return VOXTET_ERR_ARG;
   if (n_tets > 0 && (!tets || (reinterpret_cast<uintptr_t>(tets) & 15))) return VOXTET_ERR_ARG;
   if (reinterpret_cast<uintptr_t>(out) & 3) return VOXTET_ERR_ARG;
@@ -730,7 +826,7 @@ void voxtet_default_opts(voxtet_opts *o) {
 size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res) {
   (void)res;
   if (n_tets < 0 || n_verts < 0) return 0;
-  return sizeof(Header) + align256((size_t)n_verts * sizeof(int4));
+  return workspace_bytes(n_tets, n_verts, nullptr, nullptr);
 }
 
 int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
@@ -747,10 +843,10 @@ int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, 
   for (int q = 0; q < 3; ++q)
     if (!std::isfinite(grid_origin[q])) return VOXTET_ERR_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  Header *hdr = reinterpret_cast<Header *>(d_workspace);
-  int4 *verts4 = reinterpret_cast<int4 *>(reinterpret_cast<char *>(d_workspace) + sizeof(Header));
+  Workspace w;
+  workspace_bytes(n_tets, n_verts, &w, d_workspace);
   const long long W = (res + 31) / 32;
-  st = launch_prologue(hdr, d_out_bits, (long long)res * res * W, o.accumulate ? 0 : 1, stream);
+  st = launch_prologue(w, d_out_bits, (long long)res * res * W, o.accumulate ? 0 : 1, stream);
   if (st != VOXTET_OK) return st;
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
@@ -763,11 +859,11 @@ int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, 
     const double mul = use_mul ? std::ldexp(1.0, kLatticeBits - k - (e2 - 1)) : 0.0;
     k_snap<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(
         d_verts, n_verts, (double)grid_origin[0], (double)grid_origin[1], (double)grid_origin[2], h, scale, mul,
-        use_mul, verts4, hdr);
+        use_mul, w.verts4, w.hdr);
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
   }
-  return run_voxelize(verts4, n_verts, d_tets, n_tets, res, k, d_out_bits, hdr, o, stream);
+  return run_voxelize(w, n_verts, d_tets, n_tets, res, k, d_out_bits, o, stream);
 }
 
 int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_tets, int64_t n_tets, int32_t res,
@@ -780,19 +876,19 @@ int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_
   if (st != VOXTET_OK) return st;
   if (n_verts > 0 && (!d_xyz || (reinterpret_cast<uintptr_t>(d_xyz) & 3))) return VOXTET_ERR_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  Header *hdr = reinterpret_cast<Header *>(d_workspace);
-  int4 *verts4 = reinterpret_cast<int4 *>(reinterpret_cast<char *>(d_workspace) + sizeof(Header));
+  Workspace w;
+  workspace_bytes(n_tets, n_verts, &w, d_workspace);
   const long long W = (res + 31) / 32;
-  st = launch_prologue(hdr, d_out_bits, (long long)res * res * W, o.accumulate ? 0 : 1, stream);
+  st = launch_prologue(w, d_out_bits, (long long)res * res * W, o.accumulate ? 0 : 1, stream);
   if (st != VOXTET_OK) return st;
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   if (n_verts > 0) {
-    k_load_fixed<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(d_xyz, n_verts, verts4, hdr);
+    k_load_fixed<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(d_xyz, n_verts, w.verts4, w.hdr);
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
   }
-  return run_voxelize(verts4, n_verts, d_tets, n_tets, res, k, d_out_bits, hdr, o, stream);
+  return run_voxelize(w, n_verts, d_tets, n_tets, res, k, d_out_bits, o, stream);
 }
 
 int voxtet_last_status(const void *d_workspace, void *stream_) {
@@ -813,9 +909,10 @@ int voxtet_read_stats(const void *d_workspace, voxtet_stats *out, void *stream_)
   std::memset(out, 0, sizeof(*out));
   out->spans = h.spans;
   out->rows = h.rows;
-  out->fallback_rows = h.fallback_rows;
+  out->fallback_rows = h.rowq_count;
   out->degenerate_tets = h.degenerate;
   out->wide_tets = h.wide;
+  out->exact_tets = h.tetq_count;
   if (t_prof.pending) {
     float ms = 0.f;
     if (cudaEventSynchronize(t_prof.stop) != cudaSuccess ||

@@ -36,7 +36,7 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("spans", ctypes.c_uint64), ("rows", ctypes.c_uint64), ("fallback_rows", ctypes.c_uint64),
                 ("degenerate_tets", ctypes.c_uint64), ("wide_tets", ctypes.c_uint64),
-                ("kernel_ns", ctypes.c_uint64), ("reserved", ctypes.c_uint64 * 2)]
+                ("kernel_ns", ctypes.c_uint64), ("exact_tets", ctypes.c_uint64), ("reserved", ctypes.c_uint64)]
 
 
 class VoxtetError(RuntimeError):
@@ -208,4 +208,5 @@ def read_stats(workspace, stream=None) -> dict:
     if st != OK:
         raise VoxtetError(st)
     return {"spans": s.spans, "rows": s.rows, "fallback_rows": s.fallback_rows,
-            "degenerate_tets": s.degenerate_tets, "wide_tets": s.wide_tets, "kernel_ns": s.kernel_ns}
+            "degenerate_tets": s.degenerate_tets, "wide_tets": s.wide_tets, "kernel_ns": s.kernel_ns,
+            "exact_tets": s.exact_tets}
