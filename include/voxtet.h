@@ -137,6 +137,34 @@ const char *voxtet_strerror(int status);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 uint64_t voxtet_launch_count(void);
 
+/* Size of the fixed device scratch behind voxelize_tets_noalloc (16 MiB). */
+#define VOXTET_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* voxelize_tets without a workspace argument, for callers that cannot allocate
+ * device memory when they call: for example code running while a stream capture
+ * is in progress (cudaMalloc may not be called then), plugins whose host
+ * application owns the whole device-memory budget, or latency-critical loops that
+ * must not enter an allocator.  (The paper has no counterpart; this is an
+ * interface convenience.)
+ *
+ * The workspace is a fixed array of VOXTET_NOALLOC_SCRATCH_BYTES compiled into
+ * the library: every GPU that loads the library holds it until the process exits.
+ * Meshes whose voxtet_workspace_size(n_tets, n_verts, res) exceeds it are rejected
+ * with VOXTET_ERR_NOMEM before anything is launched (about 1.3M tetrahedra with
+ * 250k vertices fit).  The function itself calls no allocator; opts->profile is
+ * ignored.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current), so make that first call
+ * before any stream capture.
+ *
+ * All calls share the one array and it keeps the last call's contents; what must
+ * start at zero is cleared by every call.  Calls that overlap on the GPU (on
+ * different streams or host threads without ordering) race on it and give
+ * undefined results.  Other arguments, ownership and status codes are those of
+ * voxelize_tets. */
+int voxelize_tets_noalloc(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                          const float grid_origin[3], float voxel_size, int32_t res, uint32_t *d_out_bits,
+                          const voxtet_opts *opts, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -942,3 +942,55 @@ const char *voxtet_strerror(int s) {
 uint64_t voxtet_launch_count(void) { return g_launches.load(); }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ entry point without allocation
+//
+// voxelize_tets_noalloc runs the same kernels as voxelize_tets, but its workspace is
+// the fixed array below instead of a caller-provided buffer, for callers that cannot
+// allocate device memory at call time.  The array is part of this library's device
+// image, so every GPU that loads the library holds VOXTET_NOALLOC_SCRATCH_BYTES of it
+// until the process exits.  All calls share it and it keeps the last call's contents;
+// the kernels clear what must start at zero (header, redo bitmap) on every call.
+
+namespace voxtet {
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[VOXTET_NOALLOC_SCRATCH_BYTES];
+
+// Device address of g_noalloc_scratch, looked up once per device (the host-side name
+// of a __device__ array is only a stand-in and must not be handed to a kernel).
+static void *g_noalloc_addr[kMaxDevices];
+static std::atomic<int> g_noalloc_lock{0};
+
+static int noalloc_scratch(void *&addr) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return VOXTET_ERR_CUDA;
+  while (g_noalloc_lock.exchange(1)) {
+  }
+  int st = VOXTET_OK;
+  if (!g_noalloc_addr[dev]) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) st = VOXTET_ERR_CUDA;
+    else g_noalloc_addr[dev] = p;
+  }
+  addr = g_noalloc_addr[dev];
+  g_noalloc_lock.store(0);
+  return st;
+}
+
+}  // namespace voxtet
+
+extern "C" int voxelize_tets_noalloc(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                                     const float grid_origin[3], float voxel_size, int32_t res,
+                                     uint32_t *d_out_bits, const voxtet_opts *opts, void *stream) {
+  if (n_tets < 0 || n_verts < 0) return VOXTET_ERR_ARG;
+  if (voxtet_workspace_size(n_tets, n_verts, res) > (size_t)VOXTET_NOALLOC_SCRATCH_BYTES) return VOXTET_ERR_NOMEM;
+  voxtet_opts o;
+  resolve_opts(opts, o);
+  o.profile = 0;  // profiling would create CUDA events
+  void *ws = nullptr;
+  const int st = noalloc_scratch(ws);
+  if (st != VOXTET_OK) return st;
+  return voxelize_tets(d_verts, n_verts, d_tets, n_tets, grid_origin, voxel_size, res, d_out_bits, ws,
+                       (size_t)VOXTET_NOALLOC_SCRATCH_BYTES, &o, stream);
+}

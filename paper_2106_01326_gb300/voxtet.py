@@ -24,7 +24,9 @@ MAX_RES = 8192
 EXPORTED = (
     "voxtet_default_opts", "voxtet_workspace_size", "voxelize_tets", "voxelize_tets_fixed",
     "voxtet_last_status", "voxtet_read_stats", "voxtet_strerror", "voxtet_launch_count",
+    "voxelize_tets_noalloc",
 )
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class Opts(ctypes.Structure):
@@ -77,6 +79,9 @@ def load(path: Optional[str] = None):
         lib.voxtet_strerror.restype = ctypes.c_char_p
         lib.voxtet_launch_count.argtypes = []
         lib.voxtet_launch_count.restype = ctypes.c_uint64
+        lib.voxelize_tets_noalloc.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, i32, P,
+                                              ctypes.POINTER(Opts), P]
+        lib.voxelize_tets_noalloc.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -210,3 +215,21 @@ def read_stats(workspace, stream=None) -> dict:
     return {"spans": s.spans, "rows": s.rows, "fallback_rows": s.fallback_rows,
             "degenerate_tets": s.degenerate_tets, "wide_tets": s.wide_tets, "kernel_ns": s.kernel_ns,
             "exact_tets": s.exact_tets}
+
+
+def voxelize_noalloc(verts, tets, origin: Sequence[float], voxel_size: float, res: int, out, mode: int = 0,
+                     use_filter: bool = True, sync: bool = True, stream=None) -> int:
+    """Voxelize into ``out`` using the library's fixed device scratch instead of a
+    workspace, for callers that cannot allocate device memory when they call (see
+    voxelize_tets_noalloc in include/voxtet.h).  ``out`` must be preallocated;
+    returns the status code."""
+    torch = _torch()
+    lib = load()
+    _check_cuda_tensor(verts, "verts", torch.float32)
+    _check_cuda_tensor(tets, "tets", torch.int32)
+    _check_cuda_tensor(out, "out", torch.int32)
+    o = make_opts(mode, False, use_filter, sync)
+    org = (ctypes.c_float * 3)(*[float(x) for x in origin])
+    return int(lib.voxelize_tets_noalloc(verts.data_ptr(), verts.shape[0], tets.data_ptr(), tets.shape[0],
+                                         ctypes.byref(org), float(voxel_size), int(res), out.data_ptr(),
+                                         ctypes.byref(o), _stream_ptr(stream)))
