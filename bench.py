@@ -39,6 +39,7 @@ def parse_args():
     ap.add_argument("--span-rows", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slab", type=int, default=128, help="z-slices in the CPU oracle sample")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 256-mesh batched comparison")
     return ap.parse_args()
 
 
@@ -158,6 +159,81 @@ def run_reference(args):
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def batched_section(args, flush, stream):
+    """256 meshes (1k-100k tets, grids 32^3-128^3) as one graph-replayed batch vs one
+    call per mesh on the same stream: jobs/s, per-job completion latency, exactness."""
+    import numpy as np
+    import torch
+
+    from paper_2106_01326_gb300 import batch
+    from paper_2106_01326_gb300 import meshgen as mg
+    from paper_2106_01326_gb300 import voxtet as vt
+
+    jobs = mg.batch_workload()
+    specs, ref_out = [], []
+    for j in jobs:
+        m = batch.Mesh.from_numpy(j.verts, j.tets)
+        specs.append(batch.JobSpec(m, j.res, vt.alloc_grid(j.res), j.origin, j.voxel_size))
+        ref_out.append(vt.alloc_grid(j.res))
+    n_tets = sum(len(j.tets) for j in jobs)
+    plan = batch.Plan(batch.batch_workspace_size(specs, len(specs)), len(specs))
+    ws_single = [vt.alloc_workspace(sp.mesh.n_tets, sp.mesh.n_verts, sp.res) for sp in specs]
+
+    def run_batch():
+        st = plan.run(specs, stream=stream)
+        if st != vt.OK:
+            raise vt.VoxtetError(st)
+
+    def run_single(events=None):
+        for i, sp in enumerate(specs):
+            vt.voxelize(sp.mesh.verts, sp.mesh.tets, sp.origin, sp.voxel_size, sp.res, out=ref_out[i],
+                        workspace=ws_single[i], sync=False, stream=stream)
+            if events is not None:
+                events[i].record(stream)
+
+    for _ in range(3):
+        run_batch()
+        run_single()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b_ms, s_ms, s_lat = [], [], []
+    ev = [torch.cuda.Event(enable_timing=True) for _ in specs]
+    l0 = vt.launch_count()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e0.record(stream)
+        run_batch()
+        e1.record(stream)
+        e1.synchronize()
+        b_ms.append(e0.elapsed_time(e1))
+    launches_batch = (vt.launch_count() - l0) // max(args.steps, 1)
+    status = plan.wait()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        e0.record(stream)
+        run_single(ev)
+        e1.record(stream)
+        e1.synchronize()
+        s_ms.append(e0.elapsed_time(e1))
+        s_lat.extend(e0.elapsed_time(e) for e in ev)
+    torch.cuda.synchronize()
+    exact = all(bool(torch.equal(sp.out, r)) for sp, r in zip(specs, ref_out)) and status == [vt.OK] * len(specs)
+    plan.close()
+    bmean, smean = statistics.mean(b_ms), statistics.mean(s_ms)
+    q = lambda xs, f: float(np.percentile(np.asarray(xs), f))
+    return {
+        "workload": f"256 meshes, {n_tets} tets (log-uniform 1k-100k per mesh), grids 32^3/64^3/128^3",
+        "batched": {"jobs_per_s": len(specs) / (bmean / 1e3), "tets_per_s": n_tets / (bmean / 1e3),
+                    "ms_per_batch": bmean, "latency_ms_p50": bmean, "latency_ms_p99": bmean,
+                    "launches_per_batch": int(launches_batch), "form": "one CUDA-graph replay"},
+        "per_mesh": {"jobs_per_s": len(specs) / (smean / 1e3), "tets_per_s": n_tets / (smean / 1e3),
+                     "ms_per_batch": smean, "latency_ms_p50": q(s_lat, 50), "latency_ms_p99": q(s_lat, 99),
+                     "form": "256 voxelize_tets calls on one stream"},
+        "speedup_jobs_per_s": smean / bmean,
+        "bit_identical": exact,
+    }
 
 
 def run_ours(args):
@@ -298,6 +374,8 @@ def run_ours(args):
                   "wide_tets": int(stats["wide_tets"])},
         "clocks": clocks,
     }
+    if not args.no_batched:
+        line["batched"] = batched_section(args, flush, stream)
     if not args.no_cpu_baseline:
         import oracle
 

@@ -137,6 +137,59 @@ const char *voxtet_strerror(int status);
 /* Number of CUDA kernels this library has launched since it was loaded. */
 uint64_t voxtet_launch_count(void);
 
+/* ------------------------------------------------------------------ batches
+ *
+ * Many meshes of uneven size and resolution voxelized together: one persistent
+ * launch per kernel type covers every job (the paper voxelizes one mesh per
+ * CPU/GPU run, Section 3 "Parallelization"; Table 1 shows small meshes gain little
+ * from the GPU because of per-mesh transfer and launch overheads, which batching
+ * amortizes).  Each job has the semantics of voxelize_tets. */
+typedef struct {
+    const void *d_verts;   /* DEVICE float32 [n_verts][3], or int32 lattice coordinates if fixed_point */
+    int64_t n_verts;
+    const int32_t *d_tets; /* DEVICE int32 [n_tets][4], 16-byte aligned */
+    int64_t n_tets;
+    float origin[3];       /* grid corner (ignored if fixed_point) */
+    float voxel_size;      /* > 0 (ignored if fixed_point) */
+    int32_t res;           /* power of two in [1, VOXTET_MAX_RES] */
+    int32_t span_rows;     /* bounding-box rows per work item; 0 = opts->span_rows or automatic */
+    int32_t fixed_point;   /* 1: d_verts holds lattice coordinates as in voxelize_tets_fixed */
+    int32_t reserved;
+    uint32_t *d_out_bits;  /* DEVICE grid of this job, layout as for voxelize_tets */
+} voxtet_job;
+
+/* Bytes of device workspace (256-byte aligned) a batch of these jobs needs when
+ * the batch table is sized for max_jobs >= n_jobs jobs: a table part that grows
+ * with max_jobs plus one voxtet_workspace_size() slice per job.  0 on bad input. */
+size_t voxtet_batch_workspace_size(const voxtet_job *jobs, int32_t n_jobs, int32_t max_jobs);
+
+/* Voxelize a batch (jobs: HOST array).  Per-job argument errors are reported in
+ * job_status (HOST int32[n_jobs], may be NULL) and such jobs touch nothing; with
+ * opts->sync = 1 job_status also receives each job's device-detected status.
+ * Returns VOXTET_OK unless the batch as a whole is invalid (bad options,
+ * workspace too small: VOXTET_ERR_WORKSPACE) or CUDA fails. */
+int voxelize_tets_batched(const voxtet_job *jobs, int32_t n_jobs, void *d_workspace, size_t ws_bytes,
+                          const voxtet_opts *opts, void *stream, int32_t *job_status);
+
+/* A reusable batch plan: the first run captures the table upload and the batch
+ * kernels into a CUDA graph; later runs rewrite the table (a pinned host buffer the
+ * plan owns) and replay the graph on the caller's stream, whatever the jobs, as
+ * long as there are at most max_jobs of them and they fit the workspace.  A plan
+ * runs one batch at a time: voxtet_plan_run waits for the plan's previous run
+ * before reusing its buffer.  Use several plans (each with its own workspace) to
+ * keep several batches in flight. */
+typedef struct voxtet_plan voxtet_plan;
+
+int voxtet_plan_create(void *d_workspace, size_t ws_bytes, int32_t max_jobs, const voxtet_opts *opts,
+                       voxtet_plan **plan);
+/* Enqueue a batch on `stream`; VOXTET_ERR_NOMEM if it does not fit the workspace. */
+int voxtet_plan_run(voxtet_plan *plan, const voxtet_job *jobs, int32_t n_jobs, void *stream);
+/* 1 if the plan's last run has finished, 0 if not, negative on error (does not block). */
+int voxtet_plan_query(voxtet_plan *plan);
+/* Wait for the last run; fill job_status (HOST int32[n_jobs], may be NULL). */
+int voxtet_plan_wait(voxtet_plan *plan, int32_t *job_status);
+void voxtet_plan_destroy(voxtet_plan *plan);
+
 /* Size of the fixed device scratch behind voxelize_tets_noalloc (16 MiB). */
 #define VOXTET_NOALLOC_SCRATCH_BYTES (16u << 20)
 

@@ -36,6 +36,7 @@
 #include <atomic>
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "voxtet.h"
 #include "tet_math.cuh"
@@ -87,6 +88,7 @@ struct Params {
   int sh;           // 20 - log2(res)
   int span_rows;    // target bounding-box rows per span
   int exact_all;    // 1: every tet goes to the exact kernel
+  int cull;         // 1: skip rows outside each slice's cross-section (batched kernel)
 };
 
 // Row-queue capacity for a mesh of n_tets tets.
@@ -416,101 +418,119 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c
 constexpr int kTile = 1024;  // tets per tile
 constexpr int kPerThread = kTile / kBlock;
 
-template <bool STRICT, bool CULL>
-__global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p) {
-  __shared__ uint32_t off[kTile + 1];
-  __shared__ uint32_t warp_tot[kBlock / 32];
-  __shared__ uint32_t slice_tab[kMaxSlicesPerSpan][kBlock];
-  __shared__ unsigned long long tile_s;
+struct TileSmem {
+  uint32_t off[kTile + 1];
+  uint32_t warp_tot[kBlock / 32];
+  uint32_t slice_tab[kMaxSlicesPerSpan][kBlock];
+};
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+struct TileCounters {
   int err = 0;
-  unsigned n_degenerate = 0, n_wide = 0, n_rows = 0;
-  unsigned long long n_spans = 0;
+  unsigned degenerate = 0, wide = 0, rows = 0;
+  unsigned long long spans = 0;
+};
 
-  for (;;) {
-    if (tid == 0) tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
-    __syncthreads();
-    const long long base = (long long)tile_s * kTile;
-    if (base >= p.n_tets) break;
-
-    // (1) classification and span counts of this thread's kPerThread consecutive tets
-    uint32_t cnt[kPerThread];
-    uint32_t mine = 0;
+// Phases (1)-(4) for tets [base, base + kTile) of one mesh.  All threads of the block
+// call it; it begins and ends with the block in step.
+template <bool STRICT, bool CULL>
+__device__ __forceinline__ void process_tile(const Params &p, long long base, TileSmem &sm, TileCounters &ctr) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // (1) classification and span counts of this thread's kPerThread consecutive tets
+  uint32_t cnt[kPerThread];
+  uint32_t mine = 0;
 #pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-      const long long t = base + (long long)tid * kPerThread + k;
-      cnt[k] = t < p.n_tets ? classify_tet(p, t, err, n_degenerate, n_wide) : 0u;
-      mine += cnt[k];
-    }
-
-    // (2) block-wide exclusive prefix sum of span counts
-    uint32_t x = mine;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-      if (lane >= d) x += y;
-    }
-    if (lane == 31) warp_tot[warp] = x;
-    __syncthreads();
-    if (warp == 0) {
-      uint32_t w = lane < kBlock / 32 ? warp_tot[lane] : 0u;
-#pragma unroll
-      for (int d = 1; d < 32; d <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, d);
-        if (lane >= d) w += y;
-      }
-      if (lane < kBlock / 32) warp_tot[lane] = w;
-    }
-    __syncthreads();
-    uint32_t run = (warp ? warp_tot[warp - 1] : 0u) + x - mine;
-#pragma unroll
-    for (int k = 0; k < kPerThread; ++k) {
-      off[tid * kPerThread + k] = run;
-      run += cnt[k];
-    }
-    if (tid == kBlock - 1) off[kTile] = run;
-    __syncthreads();
-    const uint32_t total = off[kTile];
-    if (tid == 0) n_spans += total;
-
-    // (3)+(4) spans in order, so the lanes of a warp start on neighbouring tets;
-    // the tet slot of span sp is the largest u with off[u] <= sp
-    for (uint32_t sp = tid; sp < total; sp += kBlock) {
-      int a = 0, bnd = kTile - 1;
-      while (a < bnd) {
-        const int mid = (a + bnd + 1) >> 1;
-        if (off[mid] <= sp) a = mid;
-        else bnd = mid - 1;
-      }
-      const long long t = base + a;
-      int3 V[4];
-      Box bx;
-      int dummy = 0;
-      load_tet(p, t, V, dummy);
-      tet_box(V, p.sh, p.res, bx);
-      const int S = slices_per_span(p, bx.nb);
-      const int c0 = (int)(sp - off[a]) * S;
-      n_rows += run_span<STRICT, CULL>(p, t, c0, min(c0 + S, bx.nc), slice_tab);
-    }
-    __syncthreads();
+  for (int k = 0; k < kPerThread; ++k) {
+    const long long t = base + (long long)tid * kPerThread + k;
+    cnt[k] = t < p.n_tets ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide) : 0u;
+    mine += cnt[k];
   }
 
-  unsigned long long rows_w = n_rows, deg_w = n_degenerate, wide_w = n_wide;
+  // (2) block-wide exclusive prefix sum of span counts
+  uint32_t x = mine;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) sm.warp_tot[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t w = lane < kBlock / 32 ? sm.warp_tot[lane] : 0u;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+      if (lane >= d) w += y;
+    }
+    if (lane < kBlock / 32) sm.warp_tot[lane] = w;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? sm.warp_tot[warp - 1] : 0u) + x - mine;
+#pragma unroll
+  for (int k = 0; k < kPerThread; ++k) {
+    sm.off[tid * kPerThread + k] = run;
+    run += cnt[k];
+  }
+  if (tid == kBlock - 1) sm.off[kTile] = run;
+  __syncthreads();
+  const uint32_t total = sm.off[kTile];
+  if (tid == 0) ctr.spans += total;
+
+  // (3)+(4) spans in order, so the lanes of a warp start on neighbouring tets;
+  // the tet slot of span sp is the largest u with off[u] <= sp
+  for (uint32_t sp = tid; sp < total; sp += kBlock) {
+    int a = 0, bnd = kTile - 1;
+    while (a < bnd) {
+      const int mid = (a + bnd + 1) >> 1;
+      if (sm.off[mid] <= sp) a = mid;
+      else bnd = mid - 1;
+    }
+    const long long t = base + a;
+    int3 V[4];
+    Box bx;
+    int dummy = 0;
+    load_tet(p, t, V, dummy);
+    tet_box(V, p.sh, p.res, bx);
+    const int S = slices_per_span(p, bx.nb);
+    const int c0 = (int)(sp - sm.off[a]) * S;
+    ctr.rows += run_span<STRICT, CULL>(p, t, c0, min(c0 + S, bx.nc), sm.slice_tab);
+  }
+  __syncthreads();
+}
+
+// Adds a block's counters to a mesh's header: one atomic per warp and counter.
+__device__ __forceinline__ void flush_counters(Header *hdr, TileCounters &ctr) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long rows_w = ctr.rows, deg_w = ctr.degenerate, wide_w = ctr.wide;
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     rows_w += __shfl_down_sync(0xFFFFFFFFu, rows_w, d);
     deg_w += __shfl_down_sync(0xFFFFFFFFu, deg_w, d);
     wide_w += __shfl_down_sync(0xFFFFFFFFu, wide_w, d);
   }
-  err = __reduce_or_sync(0xFFFFFFFFu, err);
+  const int err = __reduce_or_sync(0xFFFFFFFFu, ctr.err);
   if (lane == 0) {
-    if (rows_w) atomicAdd(&p.hdr->rows, rows_w);
-    if (deg_w) atomicAdd(&p.hdr->degenerate, deg_w);
-    if (wide_w) atomicAdd(&p.hdr->wide, wide_w);
-    if (err) atomicOr(&p.hdr->status_bits, err);
+    if (rows_w) atomicAdd(&hdr->rows, rows_w);
+    if (deg_w) atomicAdd(&hdr->degenerate, deg_w);
+    if (wide_w) atomicAdd(&hdr->wide, wide_w);
+    if (err) atomicOr(&hdr->status_bits, err);
   }
-  if (tid == 0 && n_spans) atomicAdd(&p.hdr->spans, n_spans);
+  if (threadIdx.x == 0 && ctr.spans) atomicAdd(&hdr->spans, ctr.spans);
+  ctr = TileCounters();
+}
+
+template <bool STRICT, bool CULL>
+__global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p) {
+  __shared__ TileSmem sm;
+  __shared__ unsigned long long tile_s;
+  TileCounters ctr;
+  for (;;) {
+    if (threadIdx.x == 0) tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
+    __syncthreads();
+    const long long base = (long long)tile_s * kTile;
+    if (base >= p.n_tets) break;
+    process_tile<STRICT, CULL>(p, base, sm, ctr);
+  }
+  flush_counters(p.hdr, ctr);
 }
 
 // ------------------------------------------------------------------ the exact kernel
@@ -544,14 +564,14 @@ __device__ __forceinline__ void exact_tet(const Params &p, long long t) {
   else exact_tet_rows<STRICT, i128>(p, V, bx);
 }
 
+// The exact work of one mesh: its queued tets (a block each), queued rows (a thread
+// each) and, after a row-queue overflow, the tets flagged in its redo bitmap.
 template <bool STRICT>
-__global__ void __launch_bounds__(128) k_exact(Params p) {
+__device__ __forceinline__ void exact_job(const Params &p) {
   const unsigned n_tq = min((unsigned long long)p.hdr->tetq_count, (unsigned long long)p.n_tets);
   const unsigned n_rq_all = p.hdr->rowq_count;
   const unsigned n_rq = min(n_rq_all, p.q_cap);
-  // queued tets: one block each
   for (unsigned q = blockIdx.x; q < n_tq; q += gridDim.x) exact_tet<STRICT>(p, p.tetq[q]);
-  // queued rows: one thread each (these tets are narrow: 64-bit exact)
   const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   for (unsigned i = gtid; i < n_rq; i += gsz) {
     const RowItem it = p.rowq[i];
@@ -569,11 +589,181 @@ __global__ void __launch_bounds__(128) k_exact(Params p) {
       or_span(row, bx.i0 + lo, bx.i0 + hi);
     }
   }
-  // row-queue overflow: whole tets flagged in the redo bitmap
   if (n_rq_all > p.q_cap) {
     for (long long t = blockIdx.x; t < p.n_tets; t += gridDim.x)
       if ((p.redo[t >> 5] >> (t & 31)) & 1u) exact_tet<STRICT>(p, t);
   }
+}
+
+template <bool STRICT>
+__global__ void __launch_bounds__(128) k_exact(Params p) {
+  exact_job<STRICT>(p);
+}
+
+// ------------------------------------------------------------------ batched kernels
+//
+// A batch is a device table of jobs, each a complete single-mesh problem (its own
+// Params, snap arguments and workspace slice with the single-mesh layout).  One
+// persistent launch per kernel type covers all jobs: the voxelize kernel claims
+// tiles from one counter across the batch and finds a tile's job by bisection
+// over the per-job tile offsets.
+
+struct SnapArgs {
+  const float *verts;
+  double ox, oy, oz, h, scale, mul;
+  int use_mul;
+  int fixed;  // 1: vertices are int32 lattice coordinates (range check only)
+};
+
+struct ZeroArgs {
+  long long grid_words;
+  int clear;
+};
+
+struct JobDesc {
+  Params p;
+  SnapArgs s;
+  ZeroArgs z;
+  long long pad;
+};
+
+struct BatchHeader {
+  int n_jobs;
+  int pad0;
+  unsigned long long total_tiles;
+  unsigned long long total_verts;
+  unsigned long long tile_counter;
+  unsigned long long reserved[28];
+};
+static_assert(sizeof(BatchHeader) == 256, "batch header is 256 bytes");
+
+// Largest j in [0, n) with base[j] <= x (base ascending, base[0] = 0).
+__device__ __forceinline__ int find_job(const unsigned long long *base, int n, unsigned long long x) {
+  int a = 0, b = n - 1;
+  while (a < b) {
+    const int mid = (a + b + 1) >> 1;
+    if (base[mid] <= x) a = mid;
+    else b = mid - 1;
+  }
+  return a;
+}
+
+__global__ void k_prologue_batched(const BatchHeader *bh, const JobDesc *jobs) {
+  const int n = bh->n_jobs;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (int j = 0; j < n; ++j) {
+    const Params &p = jobs[j].p;
+    if (tid < 64) reinterpret_cast<uint32_t *>(p.hdr)[tid] = 0u;
+    const long long redo_words = (p.n_tets + 31) / 32;
+    for (long long i = tid; i < redo_words; i += stride) p.redo[i] = 0u;
+    if (jobs[j].z.clear) {
+      uint32_t *out = p.out;
+      const long long nw = jobs[j].z.grid_words;
+      if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+        uint4 *o4 = reinterpret_cast<uint4 *>(out);
+        for (long long i = tid; i < (nw >> 2); i += stride) o4[i] = make_uint4(0u, 0u, 0u, 0u);
+        for (long long i = ((nw >> 2) << 2) + tid; i < nw; i += stride) out[i] = 0u;
+      } else {
+        for (long long i = tid; i < nw; i += stride) out[i] = 0u;
+      }
+    }
+  }
+}
+
+__global__ void k_snap_batched(const BatchHeader *bh, const JobDesc *jobs, const unsigned long long *vert_base) {
+  const int n = bh->n_jobs;
+  const unsigned long long total = bh->total_verts;
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  for (unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; g < total; g += stride) {
+    const int j = find_job(vert_base, n, g);
+    const JobDesc &d = jobs[j];
+    const long long i = (long long)(g - vert_base[j]);
+    int X[3] = {0, 0, 0};
+    int flag = 0, err = 0;
+    if (d.s.fixed) {
+      const int *xyz = reinterpret_cast<const int *>(d.s.verts);
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const int x = xyz[3 * i + q];
+        if (x < -kCoordLimit || x > kCoordLimit) {
+          flag = 1;
+          err |= kErrRange;
+        } else {
+          X[q] = x;
+        }
+      }
+    } else {
+      const double o[3] = {d.s.ox, d.s.oy, d.s.oz};
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float f = d.s.verts[3 * i + q];
+        if (!isfinite(f)) {
+          flag = 1;
+          err |= kErrNan;
+          continue;
+        }
+        const double dd = __dsub_rn((double)f, o[q]);
+        const double x = d.s.use_mul ? __dmul_rn(dd, d.s.mul) : __dmul_rn(__ddiv_rn(dd, d.s.h), d.s.scale);
+        const long long r = __double2ll_rn(x);
+        if (r < -kCoordLimit || r > kCoordLimit) {
+          flag = 1;
+          err |= kErrRange;
+          continue;
+        }
+        X[q] = (int)r;
+      }
+    }
+    const_cast<int4 *>(d.p.verts4)[i] = make_int4(X[0], X[1], X[2], flag);
+    if (err) atomicOr(&d.p.hdr->status_bits, err);
+  }
+}
+
+template <bool STRICT>
+__global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
+    k_voxelize_batched(BatchHeader *bh, const JobDesc *jobs, const unsigned long long *tile_base) {
+  __shared__ TileSmem sm;
+  __shared__ Params sp;
+  __shared__ unsigned long long tile_s;
+  __shared__ int job_s;
+  TileCounters ctr;
+  const int n = bh->n_jobs;
+  const unsigned long long total = bh->total_tiles;
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      tile_s = atomicAdd(&bh->tile_counter, 1ull);
+      job_s = tile_s < total ? find_job(tile_base, n, tile_s) : -1;
+    }
+    __syncthreads();
+    const int j = job_s;
+    if (j < 0) break;
+    if (j != cur) {  // a new job: flush the previous job's counters, load its Params
+      if (cur >= 0) flush_counters(sp.hdr, ctr);
+      __syncthreads();
+      if (threadIdx.x < sizeof(Params) / sizeof(uint32_t))
+        reinterpret_cast<uint32_t *>(&sp)[threadIdx.x] = reinterpret_cast<const uint32_t *>(&jobs[j].p)[threadIdx.x];
+      __syncthreads();
+      cur = j;
+    }
+    const long long base = (long long)(tile_s - tile_base[j]) * kTile;
+    if (sp.cull) process_tile<STRICT, true>(sp, base, sm, ctr);
+    else process_tile<STRICT, false>(sp, base, sm, ctr);
+  }
+  if (cur >= 0) flush_counters(sp.hdr, ctr);
+}
+
+template <bool STRICT>
+__global__ void __launch_bounds__(128) k_exact_batched(const BatchHeader *bh, const JobDesc *jobs) {
+  const int n = bh->n_jobs;
+  for (int j = 0; j < n; ++j) exact_job<STRICT>(jobs[j].p);
+}
+
+// Copies each job's device-detected error bits into a dense array for one readback.
+__global__ void k_gather_status(const BatchHeader *bh, const JobDesc *jobs, int *status) {
+  const int n = bh->n_jobs;
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x)
+    status[j] = jobs[j].p.hdr->status_bits;
 }
 
 // ------------------------------------------------------------------ host side
@@ -940,6 +1130,321 @@ const char *voxtet_strerror(int s) {
 }
 
 uint64_t voxtet_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batches (host side)
+
+namespace voxtet {
+
+// Layout of a batch workspace: BatchHeader, JobDesc[cap], tile_base[cap + 1],
+// vert_base[cap + 1], status[cap] (each 256-byte aligned), then one single-mesh
+// workspace slice per job.  The leading part (up to the first slice) is built on
+// the host and uploaded with one copy per run.
+struct BatchLayout {
+  size_t o_table, o_tiles, o_verts, o_status, o_slices;
+};
+
+static BatchLayout batch_layout(int cap) {
+  BatchLayout L;
+  size_t o = sizeof(BatchHeader);
+  L.o_table = o;
+  o += align256((size_t)cap * sizeof(JobDesc));
+  L.o_tiles = o;
+  o += align256((size_t)(cap + 1) * sizeof(unsigned long long));
+  L.o_verts = o;
+  o += align256((size_t)(cap + 1) * sizeof(unsigned long long));
+  L.o_status = o;
+  o += align256((size_t)cap * sizeof(int));
+  L.o_slices = o;
+  return L;
+}
+
+static int check_job(const voxtet_job &j, int &k) {
+  k = log2_res(j.res);
+  if (k < 0) return VOXTET_ERR_RES;
+  if (j.n_verts < 0 || j.n_tets < 0 || j.n_verts > 0x7FFFFFFFLL || j.n_tets > 0xFFFFFFFFLL) return VOXTET_ERR_ARG;
+  if (!j.d_out_bits || (reinterpret_cast<uintptr_t>(j.d_out_bits) & 3)) return VOXTET_ERR_ARG;
+  if (j.n_tets > 0 && (!j.d_tets || (reinterpret_cast<uintptr_t>(j.d_tets) & 15))) return VOXTET_ERR_ARG;
+  if (j.n_verts > 0 && (!j.d_verts || (reinterpret_cast<uintptr_t>(j.d_verts) & 3))) return VOXTET_ERR_ARG;
+  if (j.span_rows < 0 || j.span_rows > (1 << 20)) return VOXTET_ERR_ARG;
+  if (!j.fixed_point) {
+    if (!(j.voxel_size > 0.0f) || !std::isfinite(j.voxel_size)) return VOXTET_ERR_ARG;
+    for (int q = 0; q < 3; ++q)
+      if (!std::isfinite(j.origin[q])) return VOXTET_ERR_ARG;
+  }
+  return VOXTET_OK;
+}
+
+static size_t job_slice_bytes(const voxtet_job &j, bool valid) {
+  return valid ? align256(voxtet_workspace_size(j.n_tets, j.n_verts, j.res)) : align256(sizeof(Header));
+}
+
+// Builds the host image of the table part of a batch workspace.  Returns the bytes
+// of workspace the batch needs (0 on a batch-level argument error).
+static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const voxtet_opts &o, char *ws_dev,
+                                std::vector<char> *image, int *host_status) {
+  const BatchLayout L = batch_layout(cap);
+  size_t need = L.o_slices;
+  std::vector<int> ok(n);
+  std::vector<int> kk(n);
+  for (int j = 0; j < n; ++j) {
+    const int st = check_job(jobs[j], kk[j]);
+    ok[j] = st == VOXTET_OK;
+    if (host_status) host_status[j] = st;
+    need += job_slice_bytes(jobs[j], ok[j]);
+  }
+  if (!image) return need;
+  image->assign(L.o_slices, 0);
+  char *img = image->data();
+  BatchHeader *bh = reinterpret_cast<BatchHeader *>(img);
+  JobDesc *tab = reinterpret_cast<JobDesc *>(img + L.o_table);
+  unsigned long long *tiles = reinterpret_cast<unsigned long long *>(img + L.o_tiles);
+  unsigned long long *vbase = reinterpret_cast<unsigned long long *>(img + L.o_verts);
+  size_t off = L.o_slices;
+  unsigned long long tsum = 0, vsum = 0;
+  for (int j = 0; j < n; ++j) {
+    const voxtet_job &J = jobs[j];
+    const long long nt = ok[j] ? J.n_tets : 0, nv = ok[j] ? J.n_verts : 0;
+    Workspace w;
+    workspace_bytes(nt, nv, &w, ws_dev + off);
+    off += job_slice_bytes(J, ok[j]);
+    JobDesc &d = tab[j];
+    std::memset(&d, 0, sizeof(d));
+    const int res = ok[j] ? J.res : 1;
+    const int k = ok[j] ? kk[j] : 0;
+    d.p.verts4 = w.verts4;
+    d.p.tets = reinterpret_cast<const int4 *>(J.d_tets);
+    d.p.n_tets = nt;
+    d.p.n_verts = nv;
+    d.p.out = J.d_out_bits;
+    d.p.hdr = w.hdr;
+    d.p.tetq = w.tetq;
+    d.p.rowq = w.rowq;
+    d.p.redo = w.redo;
+    d.p.q_cap = w.q_cap;
+    d.p.res = res;
+    d.p.W = (res + 31) / 32;
+    d.p.sh = kLatticeBits - k;
+    d.p.span_rows = J.span_rows > 0 ? J.span_rows : (o.span_rows > 0 ? o.span_rows : kDefaultSpanRows);
+    d.p.exact_all = o.use_filter ? 0 : 1;
+    d.p.cull = (o.row_cull == 1 || (o.row_cull == 0 && res >= kCullMinRes)) ? 1 : 0;
+    d.s.verts = reinterpret_cast<const float *>(J.d_verts);
+    d.s.fixed = J.fixed_point ? 1 : 0;
+    if (ok[j] && !J.fixed_point) {
+      d.s.ox = J.origin[0];
+      d.s.oy = J.origin[1];
+      d.s.oz = J.origin[2];
+      d.s.h = (double)J.voxel_size;
+      d.s.scale = std::ldexp(1.0, kLatticeBits - k);
+      int e2 = 0;
+      const double mant = std::frexp(d.s.h, &e2);
+      d.s.use_mul = mant == 0.5 ? 1 : 0;
+      d.s.mul = d.s.use_mul ? std::ldexp(1.0, kLatticeBits - k - (e2 - 1)) : 0.0;
+    }
+    d.z.grid_words = ok[j] ? (long long)res * res * d.p.W : 0;
+    d.z.clear = (ok[j] && !o.accumulate) ? 1 : 0;
+    tiles[j] = tsum;
+    vbase[j] = vsum;
+    tsum += (unsigned long long)((nt + kTile - 1) / kTile);
+    vsum += (unsigned long long)nv;
+  }
+  tiles[n] = tsum;
+  vbase[n] = vsum;
+  bh->n_jobs = n;
+  bh->total_tiles = tsum;
+  bh->total_verts = vsum;
+  bh->tile_counter = 0;
+  return need;
+}
+
+// Enqueues the batch kernels on `stream` (the table must already be uploaded).
+static int launch_batch(char *ws, int cap, int strict, cudaStream_t stream) {
+  DeviceInfo *dev = nullptr;
+  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+  const BatchLayout L = batch_layout(cap);
+  BatchHeader *bh = reinterpret_cast<BatchHeader *>(ws);
+  JobDesc *tab = reinterpret_cast<JobDesc *>(ws + L.o_table);
+  const unsigned long long *tiles = reinterpret_cast<const unsigned long long *>(ws + L.o_tiles);
+  const unsigned long long *vbase = reinterpret_cast<const unsigned long long *>(ws + L.o_verts);
+  int *status = reinterpret_cast<int *>(ws + L.o_status);
+  const unsigned g8 = (unsigned)dev->sms * 8;
+  k_prologue_batched<<<g8, 256, 0, stream>>>(bh, tab);
+  k_snap_batched<<<g8, 256, 0, stream>>>(bh, tab, vbase);
+  int occ = 0;
+  if (strict) {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<true>, kBlock, 0);
+    k_voxelize_batched<true><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, 0, stream>>>(bh, tab, tiles);
+    k_exact_batched<true><<<(unsigned)dev->sms * 4, kExactBlock, 0, stream>>>(bh, tab);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<false>, kBlock, 0);
+    k_voxelize_batched<false><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, 0, stream>>>(bh, tab, tiles);
+    k_exact_batched<false><<<(unsigned)dev->sms * 4, kExactBlock, 0, stream>>>(bh, tab);
+  }
+  k_gather_status<<<(cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, 256, 0, stream>>>(bh, tab, status);
+  g_launches.fetch_add(5);
+  return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
+}
+
+static int read_job_status(char *ws, int cap, int n, int *host_status, cudaStream_t stream) {
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+  if (!host_status || n == 0) return VOXTET_OK;
+  const BatchLayout L = batch_layout(cap);
+  std::vector<int> bits(n);
+  if (cudaMemcpy(bits.data(), ws + L.o_status, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return VOXTET_ERR_CUDA;
+  for (int j = 0; j < n; ++j)
+    if (host_status[j] == VOXTET_OK) host_status[j] = map_status_bits(bits[j]);
+  return VOXTET_OK;
+}
+
+}  // namespace voxtet
+
+struct voxtet_plan {
+  char *ws = nullptr;
+  size_t ws_bytes = 0;
+  int cap = 0;
+  voxtet_opts opts;
+  int device = -1;
+  char *pinned = nullptr;  // host image of the table part, uploaded by the graph
+  size_t image_bytes = 0;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool in_flight = false;
+  int n_jobs = 0;
+  std::vector<int> host_status;
+};
+
+extern "C" {
+
+size_t voxtet_batch_workspace_size(const voxtet_job *jobs, int32_t n_jobs, int32_t max_jobs) {
+  if (n_jobs < 0 || max_jobs < n_jobs || (n_jobs > 0 && !jobs)) return 0;
+  voxtet_opts o;
+  voxtet_default_opts(&o);
+  std::vector<int> st((size_t)(n_jobs > 0 ? n_jobs : 1));
+  return build_batch_image(jobs, n_jobs, max_jobs > 0 ? max_jobs : 1, o, nullptr, nullptr, st.data());
+}
+
+int voxelize_tets_batched(const voxtet_job *jobs, int32_t n_jobs, void *d_ws, size_t ws_bytes,
+                          const voxtet_opts *opts, void *stream_, int32_t *job_status) {
+  voxtet_opts o;
+  resolve_opts(opts, o);
+  int st = check_opts(o);
+  if (st != VOXTET_OK) return st;
+  if (n_jobs < 0 || (n_jobs > 0 && !jobs)) return VOXTET_ERR_ARG;
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return VOXTET_ERR_WORKSPACE;
+  const int cap = n_jobs > 0 ? n_jobs : 1;
+  std::vector<int> hs((size_t)cap, VOXTET_OK);
+  std::vector<char> image;
+  const size_t need = build_batch_image(jobs, n_jobs, cap, o, reinterpret_cast<char *>(d_ws), &image, hs.data());
+  if (need > ws_bytes) return VOXTET_ERR_WORKSPACE;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (cudaMemcpyAsync(d_ws, image.data(), image.size(), cudaMemcpyHostToDevice, stream) != cudaSuccess)
+    return VOXTET_ERR_CUDA;
+  st = launch_batch(reinterpret_cast<char *>(d_ws), cap, o.mode == 1, stream);
+  if (st != VOXTET_OK) return st;
+  if (o.sync) {
+    st = read_job_status(reinterpret_cast<char *>(d_ws), cap, n_jobs, hs.data(), stream);
+    if (st != VOXTET_OK) return st;
+    if (job_status)
+      for (int j = 0; j < n_jobs; ++j) job_status[j] = hs[j];
+  } else if (job_status) {
+    for (int j = 0; j < n_jobs; ++j) job_status[j] = hs[j];
+  }
+  return VOXTET_OK;
+}
+
+int voxtet_plan_create(void *d_ws, size_t ws_bytes, int32_t max_jobs, const voxtet_opts *opts, voxtet_plan **out) {
+  if (!out || max_jobs < 1) return VOXTET_ERR_ARG;
+  *out = nullptr;
+  if (!d_ws || (reinterpret_cast<uintptr_t>(d_ws) & 255)) return VOXTET_ERR_WORKSPACE;
+  voxtet_opts o;
+  resolve_opts(opts, o);
+  const int st = check_opts(o);
+  if (st != VOXTET_OK) return st;
+  voxtet_plan *p = new voxtet_plan();
+  p->ws = reinterpret_cast<char *>(d_ws);
+  p->ws_bytes = ws_bytes;
+  p->cap = max_jobs;
+  p->opts = o;
+  p->image_bytes = batch_layout(max_jobs).o_slices;
+  if (cudaGetDevice(&p->device) != cudaSuccess ||
+      cudaHostAlloc(reinterpret_cast<void **>(&p->pinned), p->image_bytes, cudaHostAllocDefault) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming) != cudaSuccess) {
+    voxtet_plan_destroy(p);
+    return VOXTET_ERR_CUDA;
+  }
+  *out = p;
+  return VOXTET_OK;
+}
+
+int voxtet_plan_run(voxtet_plan *p, const voxtet_job *jobs, int32_t n_jobs, void *stream_) {
+  if (!p || n_jobs < 0 || n_jobs > p->cap || (n_jobs > 0 && !jobs)) return VOXTET_ERR_ARG;
+  if (p->in_flight && cudaEventSynchronize(p->done) != cudaSuccess) return VOXTET_ERR_CUDA;
+  p->in_flight = false;
+  p->host_status.assign((size_t)(n_jobs > 0 ? n_jobs : 1), VOXTET_OK);
+  std::vector<char> image;
+  const size_t need = build_batch_image(jobs, n_jobs, p->cap, p->opts, p->ws, &image, p->host_status.data());
+  if (need > p->ws_bytes) return VOXTET_ERR_NOMEM;
+  std::memcpy(p->pinned, image.data(), p->image_bytes);
+  if (!p->exec) {  // capture the upload and the kernels once; later runs replay them
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VOXTET_ERR_CUDA;
+    cudaMemcpyAsync(p->ws, p->pinned, p->image_bytes, cudaMemcpyHostToDevice, p->cap_stream);
+    const unsigned long long before = g_launches.load();
+    const int st = launch_batch(p->ws, p->cap, p->opts.mode == 1, p->cap_stream);
+    g_launches.store(before);  // captured, not launched
+    if (cudaStreamEndCapture(p->cap_stream, &g) != cudaSuccess || st != VOXTET_OK) {
+      if (g) cudaGraphDestroy(g);
+      return VOXTET_ERR_CUDA;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&p->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+      p->exec = nullptr;
+      return VOXTET_ERR_CUDA;
+    }
+  }
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  if (cudaGraphLaunch(p->exec, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+  g_launches.fetch_add(5);
+  if (cudaEventRecord(p->done, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+  p->in_flight = true;
+  p->n_jobs = n_jobs;
+  return VOXTET_OK;
+}
+
+int voxtet_plan_wait(voxtet_plan *p, int32_t *job_status) {
+  if (!p) return VOXTET_ERR_ARG;
+  if (p->in_flight && cudaEventSynchronize(p->done) != cudaSuccess) return VOXTET_ERR_CUDA;
+  p->in_flight = false;
+  if (!job_status || p->n_jobs == 0) return VOXTET_OK;
+  const int st = read_job_status(p->ws, p->cap, p->n_jobs, p->host_status.data(), nullptr);
+  if (st != VOXTET_OK) return st;
+  for (int j = 0; j < p->n_jobs; ++j) job_status[j] = p->host_status[j];
+  return VOXTET_OK;
+}
+
+int voxtet_plan_query(voxtet_plan *p) {
+  if (!p) return VOXTET_ERR_ARG;
+  if (!p->in_flight) return 1;
+  const cudaError_t e = cudaEventQuery(p->done);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return VOXTET_ERR_CUDA;
+}
+
+void voxtet_plan_destroy(voxtet_plan *p) {
+  if (!p) return;
+  if (p->in_flight && p->done) cudaEventSynchronize(p->done);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->done) cudaEventDestroy(p->done);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->pinned) cudaFreeHost(p->pinned);
+  delete p;
+}
 
 }  // extern "C"
 

@@ -93,13 +93,40 @@ def kuhn_lattice_int(N: int) -> Tuple[np.ndarray, np.ndarray]:
 def kuhn_lattice(N: int, jitter: float = 0.0, seed: int = 0) -> Tuple[np.ndarray, np.ndarray]:
     """Jittered Kuhn lattice over [0,1]^3: (verts float32 [(N+1)^3, 3], tets int32 [6N^3, 4])."""
     ijk, tets = kuhn_lattice_int(N)
+    return _jittered_positions(ijk, N, jitter, seed), tets
+
+
+def _jittered_positions(ijk: np.ndarray, N: int, jitter: float, seed: int) -> np.ndarray:
     pos = ijk.astype(np.float64) / N
     if jitter:
         rng = np.random.Generator(np.random.PCG64(seed))
         interior = np.all((ijk > 0) & (ijk < N), axis=1)
         d = rng.uniform(-jitter, jitter, size=(int(interior.sum()), 3)) / N
         pos[interior] += d
-    return pos.astype(np.float32), tets
+    return pos.astype(np.float32)
+
+
+def clipped_kuhn_lattice(N: int, jitter: float, seed: int, sdf) -> Tuple[np.ndarray, np.ndarray]:
+    """``clip_by_centroid(*kuhn_lattice(N, jitter, seed), sdf)`` without building the
+    tets of cells that cannot keep any: a tet's centroid lies within
+    (sqrt(3)/2 + sqrt(3) jitter) cells of its cell's centre and the SDF is
+    1-Lipschitz, so cells whose centre is farther outside are skipped.  The result
+    is identical to the unfiltered recipe."""
+    n1 = N + 1
+    g = np.arange(n1, dtype=np.int64)
+    l, j, i = np.meshgrid(g, g, g, indexing="ij")
+    ijk = np.stack([i.ravel(), j.ravel(), l.ravel()], axis=1)
+    pos = _jittered_positions(ijk, N, jitter, seed)
+    c = np.arange(N, dtype=np.int64)
+    cl, cj, ci = np.meshgrid(c, c, c, indexing="ij")
+    corners = np.stack([ci.ravel(), cj.ravel(), cl.ravel()], axis=1)
+    centre = (corners.astype(np.float64) + 0.5) / N
+    reach = (np.sqrt(3.0) / 2 + np.sqrt(3.0) * abs(jitter) + 1e-6) / N
+    corners = corners[sdf(centre) < reach]
+    offs = _kuhn_cell_offsets()
+    pts = corners[:, None, None, :] + offs[None, :, :, :]
+    tets = ((pts[..., 2] * n1 + pts[..., 1]) * n1 + pts[..., 0]).reshape(-1, 4).astype(np.int32)
+    return clip_by_centroid(pos, tets, sdf)
 
 
 # ---------------------------------------------------------------- SDF clipping
@@ -232,8 +259,7 @@ def single_mesh_config(name: str) -> dict:
         res = 64
     elif name in ("torus_48", "torus_73"):
         N = 48 if name == "torus_48" else 73
-        v, t = kuhn_lattice(N, 0.25, seed)
-        v, t = clip_by_centroid(v, t, torus_sdf())
+        v, t = clipped_kuhn_lattice(N, 0.25, seed, torus_sdf())
         res = 256
     else:
         v, t = kuhn_lattice(60, 0.25, seed)
@@ -288,8 +314,7 @@ def clipped_mesh(target_tets: int, seed: int, jitter: float = 0.25) -> Tuple[np.
     probe = rng.uniform(0.0, 1.0, size=(20000, 3))
     frac = max(float((sdf(probe) < 0).mean()), 1e-3)
     N = max(2, int(round((target_tets / (6.0 * frac)) ** (1.0 / 3.0))))
-    v, t = kuhn_lattice(N, jitter, seed + 1)
-    v, t = clip_by_centroid(v, t, sdf)
+    v, t = clipped_kuhn_lattice(N, jitter, seed + 1, sdf)
     if len(t) == 0:  # pathological clip: fall back to the whole lattice
         v, t = kuhn_lattice(N, jitter, seed + 1)
     return v, t

@@ -24,7 +24,8 @@ MAX_RES = 8192
 EXPORTED = (
     "voxtet_default_opts", "voxtet_workspace_size", "voxelize_tets", "voxelize_tets_fixed",
     "voxtet_last_status", "voxtet_read_stats", "voxtet_strerror", "voxtet_launch_count",
-    "voxelize_tets_noalloc",
+    "voxelize_tets_noalloc", "voxtet_batch_workspace_size", "voxelize_tets_batched", "voxtet_plan_create",
+    "voxtet_plan_run", "voxtet_plan_query", "voxtet_plan_wait", "voxtet_plan_destroy",
 )
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
@@ -39,6 +40,13 @@ class Stats(ctypes.Structure):
     _fields_ = [("spans", ctypes.c_uint64), ("rows", ctypes.c_uint64), ("fallback_rows", ctypes.c_uint64),
                 ("degenerate_tets", ctypes.c_uint64), ("wide_tets", ctypes.c_uint64),
                 ("kernel_ns", ctypes.c_uint64), ("exact_tets", ctypes.c_uint64), ("reserved", ctypes.c_uint64)]
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("d_verts", ctypes.c_void_p), ("n_verts", ctypes.c_int64), ("d_tets", ctypes.c_void_p),
+                ("n_tets", ctypes.c_int64), ("origin", ctypes.c_float * 3), ("voxel_size", ctypes.c_float),
+                ("res", ctypes.c_int32), ("span_rows", ctypes.c_int32), ("fixed_point", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("d_out_bits", ctypes.c_void_p)]
 
 
 class VoxtetError(RuntimeError):
@@ -82,6 +90,21 @@ def load(path: Optional[str] = None):
         lib.voxelize_tets_noalloc.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, i32, P,
                                               ctypes.POINTER(Opts), P]
         lib.voxelize_tets_noalloc.restype = ctypes.c_int
+        JP = ctypes.POINTER(Job)
+        lib.voxtet_batch_workspace_size.argtypes = [JP, i32, i32]
+        lib.voxtet_batch_workspace_size.restype = sz
+        lib.voxelize_tets_batched.argtypes = [JP, i32, P, sz, ctypes.POINTER(Opts), P, ctypes.POINTER(i32)]
+        lib.voxelize_tets_batched.restype = ctypes.c_int
+        lib.voxtet_plan_create.argtypes = [P, sz, i32, ctypes.POINTER(Opts), ctypes.POINTER(P)]
+        lib.voxtet_plan_create.restype = ctypes.c_int
+        lib.voxtet_plan_run.argtypes = [P, JP, i32, P]
+        lib.voxtet_plan_run.restype = ctypes.c_int
+        lib.voxtet_plan_query.argtypes = [P]
+        lib.voxtet_plan_query.restype = ctypes.c_int
+        lib.voxtet_plan_wait.argtypes = [P, ctypes.POINTER(i32)]
+        lib.voxtet_plan_wait.restype = ctypes.c_int
+        lib.voxtet_plan_destroy.argtypes = [P]
+        lib.voxtet_plan_destroy.restype = None
         _lib = lib
         return lib
 
