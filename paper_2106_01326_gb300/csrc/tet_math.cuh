@@ -143,6 +143,37 @@ __device__ __forceinline__ void exact_setup(const int3 V[4], const Box &bx, int 
   X.Dx[3] = n3x * two_s; X.Dy[3] = n3y * two_s; X.Dz[3] = n3z * two_s;
 }
 
+// Exact affine data of constraint m alone (64-bit, requires E <= 2^20), so that a
+// caller can process one face at a time.  Face m is opposite vertex m:
+//   m = 1, 2, 3:  lam_m(P) = (P - V0) . n_m with n1 = e2 x e3, n2 = e3 x e1, n3 = e1 x e2
+//   m = 0:        lam_0(P) = (V1 - P) . ((V2 - V1) x (V3 - V1))
+// (the same four values as exact_setup; lam_0 is formed directly instead of as
+// V6 - lam_1 - lam_2 - lam_3).
+template <int M>
+__device__ __forceinline__ void slot_exact(const int3 V[4], const Box &bx, int sh, i64 &L, i64 &Dx, i64 &Dy,
+                                           i64 &Dz) {
+  const int s = 1 << (sh - 1);
+  const int3 A = M == 0 ? V[1] : V[0];
+  const int3 U = M == 0 ? V[2] : (M == 1 ? V[2] : (M == 2 ? V[3] : V[1]));
+  const int3 W = M == 0 ? V[3] : (M == 1 ? V[3] : (M == 2 ? V[1] : V[2]));
+  const i64 ux = U.x - A.x, uy = U.y - A.y, uz = U.z - A.z;
+  const i64 wx = W.x - A.x, wy = W.y - A.y, wz = W.z - A.z;
+  i64 nx = uy * wz - uz * wy, ny = uz * wx - ux * wz, nz = ux * wy - uy * wx;
+  if (M == 0) {
+    nx = -nx;
+    ny = -ny;
+    nz = -nz;
+  }
+  const i64 qx = (i64)(s + (bx.i0 << sh)) - A.x;
+  const i64 qy = (i64)(s + (bx.j0 << sh)) - A.y;
+  const i64 qz = (i64)(s + (bx.l0 << sh)) - A.z;
+  L = qx * nx + qy * ny + qz * nz;
+  const i64 two_s = (i64)1 << sh;
+  Dx = nx * two_s;
+  Dy = ny * two_s;
+  Dz = nz * two_s;
+}
+
 // Slot of each constraint: first those with Dx < 0 (upper bounds on a), then
 // Dx > 0 (lower bounds), then Dx == 0 (whole-row conditions).  slot[m] is the
 // position of constraint m; nup / nlo count the first two groups.

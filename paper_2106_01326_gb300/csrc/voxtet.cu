@@ -24,11 +24,13 @@
 //                (4) ORs the interval into the bit grid: whole 32-bit words are
 //                    stored, the two partial edge words use atomicOr since other
 //                    tets may share them.
-//                Work the filter cannot certify is queued, not solved here, so
-//                the hot loop carries no rarely used state: tets wider than 2^20
-//                lattice units or with a face parallel to x go to the tet queue,
-//                uncertain rows to the row queue (tets whose rows overflow it
-//                are flagged in the redo bitmap).
+//                Faces parallel to x only restrict which rows of a slice can
+//                hold samples; they are applied exactly when the slice table is
+//                built.  Work the filter cannot certify is queued, not solved
+//                here, so the hot loop carries no rarely used state: tets wider
+//                than 2^20 lattice units go to the tet queue, uncertain rows to
+//                the row queue (tets whose rows overflow it are flagged in the
+//                redo bitmap).
 //   k_exact      solves the queued tets and rows with exact integers and ORs
 //                them in (OR is idempotent, so redoing a row is harmless).
 #include <cuda_runtime.h>
@@ -217,19 +219,6 @@ __device__ __forceinline__ int oriented_tet(const Params &p, long long t, int3 V
   return E;
 }
 
-// True if some face has a normal with zero x component (its constraint does not
-// depend on the sample's x).  Requires E <= 2^20 (64-bit exact).
-__device__ __forceinline__ bool has_face_parallel_to_x(const int3 V[4]) {
-  const i64 e1y = V[1].y - V[0].y, e1z = V[1].z - V[0].z;
-  const i64 e2y = V[2].y - V[0].y, e2z = V[2].z - V[0].z;
-  const i64 e3y = V[3].y - V[0].y, e3z = V[3].z - V[0].z;
-  const i64 n1x = e2y * e3z - e2z * e3y;
-  const i64 n2x = e3y * e1z - e3z * e1y;
-  const i64 n3x = e1y * e2z - e1z * e2y;
-  const i64 n0x = -(n1x + n2x + n3x);
-  return n1x == 0 || n2x == 0 || n3x == 0 || n0x == 0;
-}
-
 // z-slices per span: about span_rows bounding-box rows per work item, at most
 // kMaxSlicesPerSpan (the size of each thread's slice table).
 __device__ __forceinline__ int slices_per_span(const Params &p, int nb) {
@@ -240,7 +229,7 @@ __device__ __forceinline__ int slices_per_span(const Params &p, int nb) {
 // Phase (1): classify tet t and return its span count for the filter path (0 if it
 // marks nothing or was queued for the exact kernel).
 __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, int &err, unsigned &n_degenerate,
-                                                 unsigned &n_wide) {
+                                                 unsigned &n_wide, float &work) {
   int3 V[4];
   if (!load_tet(p, t, V, err)) return 0;
   Box bx;
@@ -252,12 +241,23 @@ __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, i
   if (bx.na <= 0 || bx.nb <= 0 || bx.nc <= 0) return 0;
   const bool wide = E > kNarrowExtent;
   n_wide += wide;
-  if (wide || p.exact_all || has_face_parallel_to_x(V)) {
+  if (wide || p.exact_all) {
     const unsigned k = atomicAdd(&p.hdr->tetq_count, 1u);  // each tet is queued once: k < n_tets
     p.tetq[k] = (uint32_t)t;
     return 0;
   }
   const int S = slices_per_span(p, bx.nb);
+  // Work estimate (x-rows the span loop will visit): the tet's shadow on the yz-plane
+  // has area sum_m |n_m.x| / 4 (each shadow point is covered by two faces), which in
+  // row units is that over (2s)^2, plus about one extra row per slice.
+  {
+    const float e1y = (float)(V[1].y - V[0].y), e1z = (float)(V[1].z - V[0].z);
+    const float e2y = (float)(V[2].y - V[0].y), e2z = (float)(V[2].z - V[0].z);
+    const float e3y = (float)(V[3].y - V[0].y), e3z = (float)(V[3].z - V[0].z);
+    const float n1x = e2y * e3z - e2z * e3y, n2x = e3y * e1z - e3z * e1y, n3x = e1y * e2z - e1z * e2y;
+    const float inv = __int_as_float((127 - 2 * p.sh) << 23);  // 1 / (2s)^2, an exact power of two
+    work = (fabsf(n1x) + fabsf(n2x) + fabsf(n3x) + fabsf(n1x + n2x + n3x)) * 0.25f * inv + (float)bx.nc;
+  }
   return (uint32_t)((bx.nc + S - 1) / S);
 }
 
@@ -307,6 +307,35 @@ __device__ __forceinline__ void queue_row(const Params &p, long long t, int b, i
   }
 }
 
+// Rows allowed by a constraint that does not depend on x (a face parallel to the x
+// axis): lam = H0 + Dy b along the slice, exact.  Narrows [b_lo, b_hi] by bisection
+// on the monotone lam(b), probing only rows inside the box.
+template <bool STRICT>
+__device__ __forceinline__ void narrow_by_row_constraint(i64 H0, i64 Dy, int &b_lo, int &b_hi) {
+  if (b_lo > b_hi) return;
+  if (Dy == 0) {
+    if (!lam_ok<STRICT, i64>(H0)) b_hi = b_lo - 1;
+    return;
+  }
+  if (Dy > 0) {  // increasing: smallest b in [b_lo, b_hi + 1] that is ok
+    int x = b_lo, y = b_hi + 1;
+    while (x < y) {
+      const int mid = (x + y) >> 1;
+      if (lam_ok<STRICT, i64>(H0 + Dy * (i64)mid)) y = mid;
+      else x = mid + 1;
+    }
+    b_lo = x;
+  } else {  // decreasing: largest b in [b_lo - 1, b_hi] that is ok
+    int x = b_lo - 1, y = b_hi;
+    while (x < y) {
+      const int mid = (x + y + 1) >> 1;
+      if (lam_ok<STRICT, i64>(H0 + Dy * (i64)mid)) x = mid;
+      else y = mid - 1;
+    }
+    b_hi = x;
+  }
+}
+
 // Exact conversion of an integral float in [0, 2^22) to int without the conversion
 // unit: adding 2^23 puts the integer in the low mantissa bits.
 __device__ __forceinline__ int small_float_to_int(float f) {
@@ -326,17 +355,65 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c
   int3 V[4];
   Box bx;
   oriented_tet(p, t, V, bx);
+  // Filter data per face, built one face at a time; faces parallel to x (at most
+  // two) become neutral upper bounds here and exact row conditions below.
   float al[4], be[4], ga[4], de[4];
-  unsigned umask = 0;
+  bool up[4];
+  i64 zL0 = 0, zDy0 = 0, zDz0 = 0, zL1 = 0, zDy1 = 0, zDz1 = 0;
+  int nz = 0;
   {
-    Exact<i64> X;
-    exact_setup<i64>(V, bx, p.sh, X);
     const float fb = (float)(bx.nb - 1), fc = (float)(bx.nc - 1);
+#define VOXTET_SLOT(M)                                                                   \
+  {                                                                                      \
+    i64 L, Dx, Dy, Dz;                                                                   \
+    slot_exact<M>(V, bx, p.sh, L, Dx, Dy, Dz);                                           \
+    if (Dx != 0) {                                                                       \
+      up[M] = Dx < 0;                                                                    \
+      filter_slot(L, Dx, Dy, Dz, fb, fc, al[M], be[M], ga[M], de[M]);                    \
+    } else {                                                                             \
+      up[M] = true;                                                                      \
+      al[M] = 1.0e30f;                                                                   \
+      be[M] = ga[M] = de[M] = 0.f;                                                       \
+      if (nz == 0) {                                                                     \
+        zL0 = L; zDy0 = Dy; zDz0 = Dz;                                                   \
+      } else {                                                                           \
+        zL1 = L; zDy1 = Dy; zDz1 = Dz;                                                   \
+      }                                                                                  \
+      ++nz;                                                                              \
+    }                                                                                    \
+  }
+    VOXTET_SLOT(0)
+    VOXTET_SLOT(1)
+    VOXTET_SLOT(2)
+    VOXTET_SLOT(3)
+#undef VOXTET_SLOT
+  }
+  // Order the faces upper bounds first.  Every live tet has at least one face with
+  // Dx < 0 and one with Dx > 0 (the four gradients sum to zero and at most two are
+  // zero), so slot 0 is always an upper bound and slot 3 a lower bound; only slots 1
+  // and 2 need a flag.
+  bool up1, up2;
+  {
+    const int nup = (int)up[0] + (int)up[1] + (int)up[2] + (int)up[3];
+    int pos[4], cu = 0, cl = nup;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      umask |= (X.Dx[m] < 0 ? 1u : 0u) << m;
-      filter_slot(X.L[m], X.Dx[m], X.Dy[m], X.Dz[m], fb, fc, al[m], be[m], ga[m], de[m]);
+    for (int m = 0; m < 4; ++m) pos[m] = up[m] ? cu++ : cl++;
+    float a2[4], b2[4], g2[4], d2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      a2[q] = al[0]; b2[q] = be[0]; g2[q] = ga[0]; d2[q] = de[0];
+#pragma unroll
+      for (int m = 1; m < 4; ++m)
+        if (pos[m] == q) {
+          a2[q] = al[m]; b2[q] = be[m]; g2[q] = ga[m]; d2[q] = de[m];
+        }
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      al[q] = a2[q]; be[q] = b2[q]; ga[q] = g2[q]; de[q] = d2[q];
+    }
+    up1 = nup >= 2;
+    up2 = nup >= 3;
   }
   const int tid = threadIdx.x;
   const int ns = c1 - c0;
@@ -354,13 +431,21 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c
     for (int k = 0; k < ns; ++k) {
       int b_lo, b_hi;
       slice_rows(V, rz, s + ((bx.l0 + c0 + k) << p.sh), s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
+      if (nz > 0) narrow_by_row_constraint<STRICT>(zL0 + zDz0 * (i64)(c0 + k), zDy0, b_lo, b_hi);
+      if (nz > 1) narrow_by_row_constraint<STRICT>(zL1 + zDz1 * (i64)(c0 + k), zDy1, b_lo, b_hi);
       const int n = b_hi >= b_lo ? b_hi - b_lo + 1 : 0;
-      tab[k][tid] = (uint32_t)b_lo | ((uint32_t)n << 16);
+      tab[k][tid] = (b_hi >= b_lo ? (uint32_t)b_lo : 0u) | ((uint32_t)n << 16);
       total += (unsigned)n;
     }
   } else {
-    for (int k = 0; k < ns; ++k) tab[k][tid] = (uint32_t)bx.nb << 16;
-    total = (unsigned)(ns * bx.nb);
+    for (int k = 0; k < ns; ++k) {
+      int b_lo = 0, b_hi = bx.nb - 1;
+      if (nz > 0) narrow_by_row_constraint<STRICT>(zL0 + zDz0 * (i64)(c0 + k), zDy0, b_lo, b_hi);
+      if (nz > 1) narrow_by_row_constraint<STRICT>(zL1 + zDz1 * (i64)(c0 + k), zDy1, b_lo, b_hi);
+      const int n = b_hi >= b_lo ? b_hi - b_lo + 1 : 0;
+      tab[k][tid] = (b_hi >= b_lo ? (uint32_t)b_lo : 0u) | ((uint32_t)n << 16);
+      total += (unsigned)n;
+    }
   }
   if (total == 0) return 0;
 
@@ -401,7 +486,7 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c
         amb |= f > tl;
         v = f;
       }
-      if ((umask >> m) & 1u) hi = fminf(hi, v);
+      if (m == 0 || (m == 1 && up1) || (m == 2 && up2)) hi = fminf(hi, v);
       else lo = fmaxf(lo, -v);
     }
     if (amb) queue_row(p, t, b, c0 + k);
@@ -418,10 +503,16 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c
 constexpr int kTile = 1024;  // tets per tile
 constexpr int kPerThread = kTile / kBlock;
 
+constexpr int kSortedSpans = 4096;  // tiles with more spans run in their natural order
+constexpr int kBuckets = 32;
+
 struct TileSmem {
   uint32_t off[kTile + 1];
   uint32_t warp_tot[kBlock / 32];
   uint32_t slice_tab[kMaxSlicesPerSpan][kBlock];
+  uint16_t order[kSortedSpans];  // spans by estimated work
+  uint32_t bucket[kBuckets];
+  float wmin, wmax;
 };
 
 struct TileCounters {
@@ -437,11 +528,19 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, Ti
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // (1) classification and span counts of this thread's kPerThread consecutive tets
   uint32_t cnt[kPerThread];
+  float work[kPerThread];
   uint32_t mine = 0;
+  float wlo = 3.0e38f, whi = 0.f;
 #pragma unroll
   for (int k = 0; k < kPerThread; ++k) {
     const long long t = base + (long long)tid * kPerThread + k;
-    cnt[k] = t < p.n_tets ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide) : 0u;
+    work[k] = 0.f;
+    cnt[k] = t < p.n_tets ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide, work[k]) : 0u;
+    if (cnt[k]) {
+      work[k] /= (float)cnt[k];  // per span
+      wlo = fminf(wlo, work[k]);
+      whi = fmaxf(whi, work[k]);
+    }
     mine += cnt[k];
   }
 
@@ -471,13 +570,64 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, Ti
     run += cnt[k];
   }
   if (tid == kBlock - 1) sm.off[kTile] = run;
+  // range of the per-span work estimates over the tile
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    wlo = fminf(wlo, __shfl_xor_sync(0xFFFFFFFFu, wlo, d));
+    whi = fmaxf(whi, __shfl_xor_sync(0xFFFFFFFFu, whi, d));
+  }
+  if (tid < kBuckets) sm.bucket[tid] = 0u;
+  if (tid == 0) {
+    sm.wmin = 3.0e38f;
+    sm.wmax = 0.f;
+  }
+  __syncthreads();
+  if (lane == 0) {
+    atomicMin(reinterpret_cast<int *>(&sm.wmin), __float_as_int(wlo));  // non-negative floats order as ints
+    atomicMax(reinterpret_cast<int *>(&sm.wmax), __float_as_int(whi));
+  }
   __syncthreads();
   const uint32_t total = sm.off[kTile];
   if (tid == 0) ctr.spans += total;
 
-  // (3)+(4) spans in order, so the lanes of a warp start on neighbouring tets;
-  // the tet slot of span sp is the largest u with off[u] <= sp
-  for (uint32_t sp = tid; sp < total; sp += kBlock) {
+  // (2b) counting sort of the spans by estimated work (32 buckets over the tile's
+  // range), so that the lanes of a warp get spans of similar length
+  const bool sorted = total <= (uint32_t)kSortedSpans;
+  if (sorted) {
+    const float w0 = sm.wmin, scale = (float)kBuckets / fmaxf(sm.wmax - sm.wmin, 1e-6f);
+    int bk[kPerThread];
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+      bk[k] = min(kBuckets - 1, max(0, (int)((work[k] - w0) * scale)));
+      if (cnt[k]) atomicAdd(&sm.bucket[bk[k]], cnt[k]);
+    }
+    __syncthreads();
+    if (warp == 0) {  // exclusive prefix over the buckets
+      const uint32_t v = sm.bucket[lane];
+      uint32_t incl = v;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      sm.bucket[lane] = incl - v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < kPerThread; ++k) {
+      if (cnt[k]) {
+        const uint32_t pos = atomicAdd(&sm.bucket[bk[k]], cnt[k]);
+        const uint32_t first = sm.off[tid * kPerThread + k];
+        for (uint32_t q = 0; q < cnt[k]; ++q) sm.order[pos + q] = (uint16_t)(first + q);
+      }
+    }
+    __syncthreads();
+  }
+
+  // (3)+(4) spans (by estimated work when sorted); the tet slot of span sp is the
+  // largest u with off[u] <= sp
+  for (uint32_t i = tid; i < total; i += kBlock) {
+    const uint32_t sp = sorted ? (uint32_t)sm.order[i] : i;
     int a = 0, bnd = kTile - 1;
     while (a < bnd) {
       const int mid = (a + bnd + 1) >> 1;
