@@ -40,6 +40,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slab", type=int, default=128, help="z-slices in the CPU oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-mesh batched comparison")
+    ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) run")
+    ap.add_argument("--requests", type=int, default=10000, help="requests in the served run")
     return ap.parse_args()
 
 
@@ -178,6 +180,9 @@ def batched_section(args, flush, stream):
         specs.append(batch.JobSpec(m, j.res, vt.alloc_grid(j.res), j.origin, j.voxel_size))
         ref_out.append(vt.alloc_grid(j.res))
     n_tets = sum(len(j.tets) for j in jobs)
+    from paper_2106_01326_gb300 import autotune
+
+    tuned = autotune.tune_batch(specs, reps=2)  # per-resolution span size, untimed
     plan = batch.Plan(batch.batch_workspace_size(specs, len(specs)), len(specs))
     ws_single = [vt.alloc_workspace(sp.mesh.n_tets, sp.mesh.n_verts, sp.res) for sp in specs]
 
@@ -189,7 +194,7 @@ def batched_section(args, flush, stream):
     def run_single(events=None):
         for i, sp in enumerate(specs):
             vt.voxelize(sp.mesh.verts, sp.mesh.tets, sp.origin, sp.voxel_size, sp.res, out=ref_out[i],
-                        workspace=ws_single[i], sync=False, stream=stream)
+                        workspace=ws_single[i], sync=False, stream=stream, span_rows=sp.span_rows)
             if events is not None:
                 events[i].record(stream)
 
@@ -232,8 +237,54 @@ def batched_section(args, flush, stream):
                      "ms_per_batch": smean, "latency_ms_p50": q(s_lat, 50), "latency_ms_p99": q(s_lat, 99),
                      "form": "256 voxelize_tets calls on one stream"},
         "speedup_jobs_per_s": smean / bmean,
+        "span_rows_by_res": {str(r): v["span_rows"] for r, v in tuned.items()},
         "bit_identical": exact,
     }
+
+
+def served_section(args):
+    """Continuous batching of a Poisson request stream over a pool of 16 device-resident
+    meshes (1k-2M tets, log-uniform) at 64^3-512^3: capacity (all requests queued at
+    once) and latency at 80% of that rate; every 25th result is checked bit for bit
+    against the same request voxelized alone."""
+    import torch
+
+    from paper_2106_01326_gb300 import batch, server
+    from paper_2106_01326_gb300 import meshgen as mg
+    from paper_2106_01326_gb300 import voxtet as vt
+
+    pool = [batch.Mesh.from_numpy(v, t) for v, t in mg.mesh_pool(16, seed=1004, tets_lo=1000, tets_hi=2000000)]
+    res_set = (64, 128, 256, 512)
+    alone = {}
+    checked = [0, 0]
+
+    def check(tk, grid):
+        if tk.rid % 25:
+            return
+        key = (tk.mesh_id, tk.res)
+        if key not in alone:
+            m = pool[tk.mesh_id]
+            alone[key] = vt.voxelize(m.verts, m.tets, (0, 0, 0), 1.0 / tk.res, tk.res)
+        checked[0] += 1
+        checked[1] += int(torch.equal(grid, alone[key]))
+
+    def make_server():
+        return server.Server(pool, arena_bytes=4 << 30, n_slots=3, slot_workspace_bytes=512 << 20, max_jobs=64,
+                             on_result=check)
+
+    n = args.requests
+    sat_reqs = mg.poisson_stream(n, rate_per_s=1.0, n_pool=len(pool), seed=1004, resolutions=res_set)
+    srv = make_server()
+    srv.serve(sat_reqs[: min(n, 200)], realtime=False)  # warm-up: graph capture, first launches
+    torch.cuda.synchronize()
+    cap = srv.serve(sat_reqs, realtime=False).summary()
+    rate = 0.8 * cap["jobs_per_s"]
+    reqs = mg.poisson_stream(n, rate_per_s=rate, n_pool=len(pool), seed=1004, resolutions=res_set)
+    rt = srv.serve(reqs, realtime=True).summary()
+    srv.close()
+    return {"workload": f"{n} Poisson requests over 16 pooled meshes ({sum(m.n_tets for m in pool)} tets), "
+                        f"grids {res_set}", "capacity": cap, "poisson_at_0.8_capacity": dict(rt, rate_per_s=rate),
+            "sampled_exact": f"{checked[1]}/{checked[0]}", "slots": 3, "arena_GiB": 4}
 
 
 def run_ours(args):
@@ -269,9 +320,18 @@ def run_ours(args):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
+    # launch shape: the autotuner times span sizes and row culling on this mesh (untimed)
+    from paper_2106_01326_gb300 import autotune
+
+    if args.span_rows > 0:
+        span_rows, row_cull, tuned = args.span_rows, 0, None
+    else:
+        tuned = autotune.tune(verts, tets, cfg["origin"], cfg["voxel_size"], res, reps=3)
+        span_rows, row_cull = tuned["span_rows"], tuned["row_cull"]
+
     def step():
         vt.voxelize(verts, tets, cfg["origin"], cfg["voxel_size"], res, out=grid, workspace=ws, sync=False,
-                    span_rows=args.span_rows, profile=True, stream=stream)
+                    span_rows=span_rows, row_cull=row_cull, profile=True, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -322,7 +382,7 @@ def run_ours(args):
         d_verts.copy_(h_verts, non_blocking=True)
         d_tets.copy_(h_tets, non_blocking=True)
         vt.voxelize(d_verts, d_tets, cfg["origin"], cfg["voxel_size"], res, out=grid, workspace=ws, sync=False,
-                    span_rows=args.span_rows, stream=stream)
+                    span_rows=span_rows, row_cull=row_cull, stream=stream)
         h_grid.copy_(grid, non_blocking=True)
 
     for _ in range(2):
@@ -361,7 +421,8 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}: 60^3 jittered Kuhn lattice, 2% slivers, {n_t} tets, {n_v} verts "
                                f"-> {res}^3 bit grid", "res": res, "n_tets": n_t, "n_verts": n_v,
                    "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}",
-                   "span_rows": args.span_rows or "auto"},
+                   "span_rows": span_rows, "row_cull": {0: "auto", 1: "on", 2: "off"}[row_cull],
+                   "launch_shape": "autotuned" if tuned else "given"},
         "gvox_per_s": gvox,
         "e2e": {"value": world * n_t * args.steps / (e2e_total / 1000.0), "unit": UNIT,
                 "h2d_bytes_per_step": 12 * n_v + 16 * n_t, "d2h_bytes_per_step": res ** 3 // 8},
@@ -376,6 +437,8 @@ def run_ours(args):
     }
     if not args.no_batched:
         line["batched"] = batched_section(args, flush, stream)
+    if not args.no_served:
+        line["served"] = served_section(args)
     if not args.no_cpu_baseline:
         import oracle
 

@@ -50,7 +50,10 @@ namespace voxtet {
 #endif
 
 constexpr int kBlock = 256;             // threads per block
-constexpr int kDefaultSpanRows = 128;   // bounding-box rows per span (whole z-slices)
+// Bounding-box rows per span (whole z-slices) when the caller does not choose: measured
+// on GB300, 256 is best up to 512^3 grids and 128 from 1024^3 (smaller spans balance
+// the larger boxes of fine grids better).
+static __host__ __device__ int default_span_rows(int res) { return res >= 1024 ? 128 : 256; }
 constexpr int kCullMinRes = 256;        // automatic row culling from this resolution up
 
 // Workspace header (first 256 bytes of the workspace).
@@ -1079,7 +1082,7 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     p.res = res;
     p.W = (res + 31) / 32;
     p.sh = kLatticeBits - k;
-    p.span_rows = o.span_rows > 0 ? o.span_rows : kDefaultSpanRows;
+    p.span_rows = o.span_rows > 0 ? o.span_rows : default_span_rows(res);
     p.exact_all = o.use_filter ? 0 : 1;
     const long long tiles = (n_tets + kTile - 1) / kTile;
     const bool cull = o.row_cull == 1 || (o.row_cull == 0 && res >= kCullMinRes);
@@ -1376,7 +1379,7 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
     d.p.res = res;
     d.p.W = (res + 31) / 32;
     d.p.sh = kLatticeBits - k;
-    d.p.span_rows = J.span_rows > 0 ? J.span_rows : (o.span_rows > 0 ? o.span_rows : kDefaultSpanRows);
+    d.p.span_rows = J.span_rows > 0 ? J.span_rows : (o.span_rows > 0 ? o.span_rows : default_span_rows(res));
     d.p.exact_all = o.use_filter ? 0 : 1;
     d.p.cull = (o.row_cull == 1 || (o.row_cull == 0 && res >= kCullMinRes)) ? 1 : 0;
     d.s.verts = reinterpret_cast<const float *>(J.d_verts);
