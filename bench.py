@@ -52,6 +52,36 @@ def dist_env():
     return rank, world, local
 
 
+def kernel_source_digest() -> str:
+    """SHA-256 over the CUDA sources; a recorded ncu traffic figure is valid only for it."""
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in ("voxtet.cu", "tet_math.cuh"):
+        with open(os.path.join(ROOT, "paper_2106_01326_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per k_voxelize launch from profiles/k_voxelize_traffic.txt (one ncu
+    capture of this benchmark's command), or None if it was taken on other sources or
+    another workload."""
+    p = os.path.join(ROOT, "profiles", "k_voxelize_traffic.txt")
+    try:
+        kv = {}
+        with open(p) as f:
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("source_sha256") != kernel_source_digest() or kv.get("workload") != workload:
+            return None
+        return int(kv["dram_bytes_per_launch"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -428,7 +458,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": 12 * n_v + 16 * n_t, "d2h_bytes_per_step": res ** 3 // 8},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "k_voxelize", "kernel_ms": kmean,
+                     "traffic": recorded_traffic(args.workload), "kernel": "k_voxelize", "kernel_ms": kmean,
                      "algorithmic_bytes": alg_bytes, "peak_source": peak_kind},
         "stats": {"rows": int(stats["rows"]), "spans": int(stats["spans"]),
                   "fallback_rows": int(stats["fallback_rows"]), "degenerate_tets": int(stats["degenerate_tets"]),

@@ -98,7 +98,7 @@ void voxtet_default_opts(voxtet_opts *opts);
  * be 256-byte aligned).  It holds a 256-byte status/counter header, the snapped
  * vertices (16 B per vertex), a queue of tetrahedra for the exact solver (4 B per
  * tetrahedron), a queue of rows the filter could not certify (8 B per entry,
- * max(65536, n_tets / 4) entries) and a redo bitmap (1 bit per tetrahedron).
+ * max(65536, n_tets) entries) and a redo bitmap (1 bit per tetrahedron).
  * Returns 0 for negative sizes. */
 size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res);
 
@@ -203,8 +203,8 @@ void voxtet_plan_destroy(voxtet_plan *plan);
  * The workspace is a fixed array of VOXTET_NOALLOC_SCRATCH_BYTES compiled into
  * the library: every GPU that loads the library holds it until the process exits.
  * Meshes whose voxtet_workspace_size(n_tets, n_verts, res) exceeds it are rejected
- * with VOXTET_ERR_NOMEM before anything is launched (about 1.3M tetrahedra with
- * 250k vertices fit).  The function itself calls no allocator; opts->profile is
+ * with VOXTET_ERR_NOMEM before anything is launched (about 1M tetrahedra with
+ * 200k vertices fit).  The function itself calls no allocator; opts->profile is
  * ignored.  The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, with that device current), so make that first call
  * before any stream capture.

@@ -98,8 +98,7 @@ struct Params {
 
 // Row-queue capacity for a mesh of n_tets tets.
 static unsigned long long row_queue_capacity(long long n_tets) {
-  const long long q = n_tets / 4;
-  return (unsigned long long)(q < 65536 ? 65536 : q);
+  return (unsigned long long)(n_tets < 65536 ? 65536 : n_tets);
 }
 
 // ------------------------------------------------------------------ small kernels

@@ -170,6 +170,7 @@ class Server:
         batches = 0
         stalls = 0
         stalled = False
+        self.arena.peak = self.arena.used
         t0 = time.perf_counter()
         while finished < n:
             now = time.perf_counter() - t0
