@@ -52,6 +52,22 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(value_ms: float, dist=None, device=None) -> float:
+    """The largest per-rank time (the job takes as long as its slowest rank)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value_ms)
+    import torch
+
+    t = torch.tensor([float(value_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, steps: int, total_ms_max: float) -> float:
+    """Units all ranks processed per second of the slowest rank (weak scaling)."""
+    return world * units_per_rank * steps / (total_ms_max / 1000.0)
+
+
 def kernel_source_digest() -> str:
     """SHA-256 over the CUDA sources; a recorded ncu traffic figure is valid only for it."""
     import hashlib
@@ -391,11 +407,8 @@ def run_ours(args):
     launches = vt.launch_count() - launches0
     torch.cuda.synchronize()
     clocks = sampler.stop() if sampler else None
-    total_ms = sum(step_ms)
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
         dist.barrier()
     st = vt.last_status(ws)
     if st != vt.OK:
@@ -427,18 +440,14 @@ def run_ours(args):
         e1.record(stream)
         e1.synchronize()
         e2e_ms.append(e0.elapsed_time(e1))
-    e2e_total = sum(e2e_ms)
-    if dist is not None:
-        t = torch.tensor([e2e_total], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
+    e2e_total = max_over_ranks(sum(e2e_ms), dist, dev)
 
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return 0
 
-    value = world * n_t * args.steps / (total_ms / 1000.0)
+    value = whole_job_rate(n_t, world, args.steps, total_ms)
     gvox = world * (res ** 3) * args.steps / (total_ms / 1000.0) / 1e9
     kmean = statistics.mean(kern_ms)
     alg_bytes = 16 * n_t + 12 * n_v + res ** 3 // 8
@@ -454,7 +463,7 @@ def run_ours(args):
                    "span_rows": span_rows, "row_cull": {0: "auto", 1: "on", 2: "off"}[row_cull],
                    "launch_shape": "autotuned" if tuned else "given"},
         "gvox_per_s": gvox,
-        "e2e": {"value": world * n_t * args.steps / (e2e_total / 1000.0), "unit": UNIT,
+        "e2e": {"value": whole_job_rate(n_t, world, args.steps, e2e_total), "unit": UNIT,
                 "h2d_bytes_per_step": 12 * n_v + 16 * n_t, "d2h_bytes_per_step": res ** 3 // 8},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
