@@ -94,6 +94,7 @@ struct Params {
   int span_rows;    // target bounding-box rows per span
   int exact_all;    // 1: every tet goes to the exact kernel
   int cull;         // 1: skip rows outside each slice's cross-section (batched kernel)
+  long long big_tiles;  // single-mesh launch: tiles of kTile tets before the kSmallTile tail
 };
 
 // Row-queue capacity for a mesh of n_tets tets.
@@ -171,21 +172,33 @@ __global__ void k_load_fixed(const int *__restrict__ xyz, long long n, int4 *__r
 // ------------------------------------------------------------------ OR writes
 
 // OR the samples x0..x1 (inclusive, absolute x indices) into one row of words.
+// Used by the exact kernel; any word may be shared with other tets.
 __device__ __forceinline__ void or_span(uint32_t *__restrict__ row, int x0, int x1) {
   const int w0 = x0 >> 5, w1 = x1 >> 5;
   const uint32_t m0 = 0xFFFFFFFFu << (x0 & 31);
   const uint32_t m1 = 0xFFFFFFFFu >> (31 - (x1 & 31));
   if (w0 == w1) {
-    const uint32_t m = m0 & m1;
-    if (m == 0xFFFFFFFFu) row[w0] = m;
-    else atomicOr(row + w0, m);
+    atomicOr(row + w0, m0 & m1);
     return;
   }
-  if (m0 == 0xFFFFFFFFu) row[w0] = m0;
-  else atomicOr(row + w0, m0);
-  for (int w = w0 + 1; w < w1; ++w) row[w] = 0xFFFFFFFFu;
-  if (m1 == 0xFFFFFFFFu) row[w1] = m1;
-  else atomicOr(row + w1, m1);
+  atomicOr(row + w0, m0);
+  for (int w = w0 + 1; w < w1; ++w) row[w] = 0xFFFFFFFFu;  // whole words: a plain store is an OR
+  atomicOr(row + w1, m1);
+}
+
+// The same for the hot loop, shaped to keep the lanes of a warp together: the first
+// word is always ORed (a zero mask when `live` is false), the second word only under
+// a predicate, and the rarely needed run of whole middle words behind a branch.
+__device__ __forceinline__ void or_span_lanes(uint32_t *__restrict__ row, int x0, int x1, bool live) {
+  const int w0 = x0 >> 5, w1 = x1 >> 5;
+  const uint32_t m1 = 0xFFFFFFFFu >> (31 - (x1 & 31));
+  uint32_t m0 = 0xFFFFFFFFu << (x0 & 31);
+  m0 = w0 == w1 ? (m0 & m1) : m0;
+  if (live) atomicOr(row + w0, m0);
+  if (live && w1 != w0) atomicOr(row + w1, m1);
+  if (live && w1 > w0 + 1) {
+    for (int w = w0 + 1; w < w1; ++w) row[w] = 0xFFFFFFFFu;
+  }
 }
 
 // ------------------------------------------------------------------ per-tet helpers
@@ -221,11 +234,14 @@ __device__ __forceinline__ int oriented_tet(const Params &p, long long t, int3 V
   return E;
 }
 
-// z-slices per span: about span_rows bounding-box rows per work item, at most
-// kMaxSlicesPerSpan (the size of each thread's slice table).
-__device__ __forceinline__ int slices_per_span(const Params &p, int nb) {
-  const int S = p.span_rows / nb;
-  return S < 1 ? 1 : (S > 16 ? 16 : S);
+// z-slices per span: the tet's nc slices are split into equal spans of about
+// span_rows bounding-box rows each, at most kMaxSlicesPerSpan (the size of each
+// thread's slice table).  Equal spans keep the per-span work estimate meaningful.
+__device__ __forceinline__ int slices_per_span(const Params &p, int nb, int nc) {
+  int S = p.span_rows / nb;
+  S = S < 1 ? 1 : (S > 16 ? 16 : S);
+  const int n = (nc + S - 1) / S;
+  return (nc + n - 1) / n;
 }
 
 // Phase (1): classify tet t and return its span count for the filter path (0 if it
@@ -248,7 +264,7 @@ __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, i
     p.tetq[k] = (uint32_t)t;
     return 0;
   }
-  const int S = slices_per_span(p, bx.nb);
+  const int S = slices_per_span(p, bx.nb, bx.nc);
   // Work estimate (x-rows the span loop will visit): the tet's shadow on the yz-plane
   // has area sum_m |n_m.x| / 4 (each shadow point is covered by two faces), which in
   // row units is that over (2s)^2, plus about one extra row per slice.
@@ -263,31 +279,59 @@ __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, i
   return (uint32_t)((bx.nc + S - 1) / S);
 }
 
-// Rows of slice Z that can hold samples: the y-extent of the tet's cross-section at
-// that z, from the crossing points of its 6 edges, widened by 2 lattice units (each
-// crossing point's float error is below 0.7 units: the edge parameter carries at
-// most two roundings, |dy| < 2^22 and |y| < 2^21), so the range is a superset of
-// the non-empty rows.  rz[e] = 1 / (z_q - z_p) of edge e (0 for horizontal edges,
-// which are skipped: their end points are covered by the other edges).
-__device__ __forceinline__ void slice_rows(const int3 V[4], const float rz[6], int Z, int s, int sh, int j0, int nb,
-                                           int &b_lo, int &b_hi) {
-  float ymin = 3.0e38f, ymax = -3.0e38f;
+// Edge lines of a tet for the per-slice row range, with the vertices sorted by z
+// (z0 <= z1 <= z2 <= z3).  Edge (p, q) crosses the plane at height Z at
+// y = y_p + (Z - z_p) k with k = (y_q - y_p) / (z_q - z_p) (k = 0 for horizontal edges,
+// whose end points the other edges also reach).  Z - z_p is exact in float
+// (|Z|, |z_p| <= 2^21) and k carries one rounding, so each crossing point is within
+// u 2^22 + u 2^21 < 0.4 lattice units of the true one.  Edge order: 01 02 03 12 13 23.
+struct EdgeLines {
+  float zp[6], yp[6], k[6];
+  int z1, z2;
+};
+
+__device__ __forceinline__ void edge_lines(const int3 V[4], EdgeLines &E) {
+  int z[4] = {V[0].z, V[1].z, V[2].z, V[3].z};
+  int y[4] = {V[0].y, V[1].y, V[2].y, V[3].y};
+#define VOXTET_CSWAP(a, b)                                  \
+  if (z[b] < z[a]) {                                        \
+    const int tz = z[a], ty = y[a];                         \
+    z[a] = z[b]; y[a] = y[b]; z[b] = tz; y[b] = ty;         \
+  }
+  VOXTET_CSWAP(0, 1)
+  VOXTET_CSWAP(2, 3)
+  VOXTET_CSWAP(0, 2)
+  VOXTET_CSWAP(1, 3)
+  VOXTET_CSWAP(1, 2)
+#undef VOXTET_CSWAP
 #pragma unroll
   for (int e = 0; e < 6; ++e) {
     const int pi = e < 3 ? 0 : (e < 5 ? 1 : 2);
     const int qi = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
-    const int zp = V[pi].z, zq = V[qi].z;
-    if (zp != zq && min(zp, zq) <= Z && Z <= max(zp, zq)) {
-      const float tpar = (float)(Z - zp) * rz[e];
-      const float y = __fmaf_rn(tpar, (float)(V[qi].y - V[pi].y), (float)V[pi].y);
+    const int dz = z[qi] - z[pi];
+    E.zp[e] = (float)z[pi];
+    E.yp[e] = (float)y[pi];
+    E.k[e] = dz != 0 ? __fdiv_rn((float)(y[qi] - y[pi]), (float)dz) : 0.f;
+  }
+  E.z1 = z[1];
+  E.z2 = z[2];
+}
+
+// Candidate rows [b_lo, b_hi] of the slice at height Z (inside the tet's z-range):
+// the cross-section's y-extent, widened by 2 lattice units, in row indices.
+__device__ __forceinline__ void slice_rows_sorted(const EdgeLines &E, int Z, int s, int sh, int j0, int nb,
+                                                  int &b_lo, int &b_hi) {
+  const float Zf = (float)Z;
+  const bool le1 = Z <= E.z1, le2 = Z <= E.z2, ge1 = Z >= E.z1, ge2 = Z >= E.z2;
+  const bool valid[6] = {le1, le2, true, ge1 && le2, ge1, ge2};
+  float ymin = 3.0e38f, ymax = -3.0e38f;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) {
+    const float y = __fmaf_rn(Zf - E.zp[e], E.k[e], E.yp[e]);
+    if (valid[e]) {
       ymin = fminf(ymin, y);
       ymax = fmaxf(ymax, y);
     }
-  }
-  if (ymin > ymax) {  // cannot happen for a slice inside the box; stay conservative
-    b_lo = 0;
-    b_hi = nb - 1;
-    return;
   }
   const int ylo = (int)floorf(ymin) - 2, yhi = (int)ceilf(ymax) + 2;
   b_lo = max(((ylo + s - 1) >> sh) - j0, 0);
@@ -338,6 +382,47 @@ __device__ __forceinline__ void narrow_by_row_constraint(i64 H0, i64 Dy, int &b_
   }
 }
 
+// Uncertain rows are first collected in a per-block shared-memory buffer and moved
+// to the global row queue with one atomic per tile, so that thousands of threads do
+// not contend on the queue counter.
+constexpr int kStage = 512;
+struct RowStage {
+  RowItem items[kStage];
+  uint32_t n;
+  uint32_t base;
+};
+
+__device__ __forceinline__ void queue_row_staged(const Params &p, RowStage &st, long long t, int b, int c) {
+  const uint32_t k = atomicAdd(&st.n, 1u);
+  if (k < (uint32_t)kStage) {
+    RowItem it;
+    it.tet = (uint32_t)t;
+    it.b = (uint16_t)b;
+    it.c = (uint16_t)c;
+    st.items[k] = it;
+  } else {
+    queue_row(p, t, b, c);
+  }
+}
+
+// Moves a block's staged rows to the global queue (all threads of the block call it).
+__device__ __forceinline__ void flush_stage(const Params &p, RowStage &st) {
+  __syncthreads();
+  const uint32_t n = min(st.n, (uint32_t)kStage);
+  if (n) {
+    if (threadIdx.x == 0) st.base = atomicAdd(&p.hdr->rowq_count, n);
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+      const unsigned k = st.base + i;
+      const RowItem it = st.items[i];
+      if (k < p.q_cap) p.rowq[k] = it;
+      else atomicOr(&p.redo[it.tet >> 5], 1u << (it.tet & 31));
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) st.n = 0;
+}
+
 // Exact conversion of an integral float in [0, 2^22) to int without the conversion
 // unit: adding 2^23 puts the integer in the low mantissa bits.
 __device__ __forceinline__ int small_float_to_int(float f) {
@@ -352,11 +437,13 @@ constexpr int kMaxSlicesPerSpan = 16;
 // walks all candidate rows, so the lanes of a warp stay in step across slices.
 // Returns the rows visited.
 template <bool STRICT, bool CULL>
-__device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c0, int c1,
-                                             uint32_t (*tab)[kBlock]) {
-  int3 V[4];
-  Box bx;
-  oriented_tet(p, t, V, bx);
+__device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 V[4], const Box &bx, int c0, int c1,
+                                             uint32_t (*tab)[kBlock], RowStage &stage) {
+  if (v6_sign(V, kNarrowExtent) < 0) {  // orient (the tet is narrow: 64-bit sign)
+    const int3 tmp = V[2];
+    V[2] = V[3];
+    V[3] = tmp;
+  }
   // Filter data per face, built one face at a time; faces parallel to x (at most
   // two) become neutral upper bounds here and exact row conditions below.
   float al[4], be[4], ga[4], de[4];
@@ -419,52 +506,42 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c
   }
   const int tid = threadIdx.x;
   const int ns = c1 - c0;
+  // slice table: only slices with candidate rows, packed k | b_lo << 4 | n << 18
+  // (k < 16 slices, b_lo and n < 2^14)
   unsigned total = 0;
-  if (CULL) {
-    float rz[6];
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      const int pi = e < 3 ? 0 : (e < 5 ? 1 : 2);
-      const int qi = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
-      const int dz = V[qi].z - V[pi].z;
-      rz[e] = dz != 0 ? __frcp_rn((float)dz) : 0.f;
-    }
+  int nt = 0;
+  {
+    EdgeLines EL;
+    if (CULL) edge_lines(V, EL);
     const int s = 1 << (p.sh - 1);
     for (int k = 0; k < ns; ++k) {
-      int b_lo, b_hi;
-      slice_rows(V, rz, s + ((bx.l0 + c0 + k) << p.sh), s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
-      if (nz > 0) narrow_by_row_constraint<STRICT>(zL0 + zDz0 * (i64)(c0 + k), zDy0, b_lo, b_hi);
-      if (nz > 1) narrow_by_row_constraint<STRICT>(zL1 + zDz1 * (i64)(c0 + k), zDy1, b_lo, b_hi);
-      const int n = b_hi >= b_lo ? b_hi - b_lo + 1 : 0;
-      tab[k][tid] = (b_hi >= b_lo ? (uint32_t)b_lo : 0u) | ((uint32_t)n << 16);
-      total += (unsigned)n;
-    }
-  } else {
-    for (int k = 0; k < ns; ++k) {
       int b_lo = 0, b_hi = bx.nb - 1;
+      if (CULL) slice_rows_sorted(EL, s + ((bx.l0 + c0 + k) << p.sh), s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
       if (nz > 0) narrow_by_row_constraint<STRICT>(zL0 + zDz0 * (i64)(c0 + k), zDy0, b_lo, b_hi);
       if (nz > 1) narrow_by_row_constraint<STRICT>(zL1 + zDz1 * (i64)(c0 + k), zDy1, b_lo, b_hi);
-      const int n = b_hi >= b_lo ? b_hi - b_lo + 1 : 0;
-      tab[k][tid] = (b_hi >= b_lo ? (uint32_t)b_lo : 0u) | ((uint32_t)n << 16);
-      total += (unsigned)n;
+      if (b_hi >= b_lo) {
+        const int n = b_hi - b_lo + 1;
+        tab[nt][tid] = (uint32_t)k | ((uint32_t)b_lo << 4) | ((uint32_t)n << 18);
+        ++nt;
+        total += (unsigned)n;
+      }
     }
   }
   if (total == 0) return 0;
 
-  // walk the candidate rows slice by slice
-  int k = -1, b = 0, b_end = 0;
+  // walk the candidate rows slice by slice; moving to the next table entry is a short
+  // straight-line step (no empty slices in the table)
+  int m_tab = 0, b = 0, b_end = 0;
   float bf = 0.f, ac[4];
   uint32_t *row = p.out;
   const float fhi0 = (float)(bx.na - 1);
   for (unsigned r = 0; r < total; ++r) {
-    if (b == b_end) {  // next non-empty slice
-      uint32_t e;
-      do {
-        ++k;
-        e = tab[k][tid];
-      } while ((e >> 16) == 0u);
-      b = (int)(e & 0xFFFFu);
-      b_end = b + (int)(e >> 16);
+    if (b == b_end) {
+      const uint32_t e = tab[m_tab][tid];
+      ++m_tab;
+      const int k = (int)(e & 15u);
+      b = (int)((e >> 4) & 0x3FFFu);
+      b_end = b + (int)(e >> 18);
       bf = (float)b;
       const float cf = (float)(c0 + k);
 #pragma unroll
@@ -491,8 +568,13 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c
       if (m == 0 || (m == 1 && up1) || (m == 2 && up2)) hi = fminf(hi, v);
       else lo = fmaxf(lo, -v);
     }
-    if (amb) queue_row(p, t, b, c0 + k);
-    else if (lo <= hi) or_span(row, bx.i0 + small_float_to_int(lo), bx.i0 + small_float_to_int(hi));
+    const bool live = !amb && lo <= hi;
+    // lo, hi are integral floats in [0, na - 1] when live; clamp so that the word
+    // arithmetic below stays inside the row when not
+    const int x0 = bx.i0 + small_float_to_int(fminf(fmaxf(lo, 0.f), fhi0));
+    const int x1 = bx.i0 + small_float_to_int(fminf(fmaxf(hi, 0.f), fhi0));
+    or_span_lanes(row, x0, x1, live);
+    if (amb) queue_row_staged(p, stage, t, b, c0 + (int)(tab[m_tab - 1][tid] & 15u));
     ++b;
     bf += 1.f;
     row += p.W;
@@ -502,7 +584,8 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int c
 
 // ------------------------------------------------------------------ the fused kernel
 
-constexpr int kTile = 1024;  // tets per tile
+constexpr int kTile = 1024;      // tets per tile
+constexpr int kSmallTile = 256;  // tets per tile at the end of a single-mesh launch
 constexpr int kPerThread = kTile / kBlock;
 
 constexpr int kSortedSpans = 4096;  // tiles with more spans run in their natural order
@@ -515,6 +598,7 @@ struct TileSmem {
   uint16_t order[kSortedSpans];  // spans by estimated work
   uint32_t bucket[kBuckets];
   float wmin, wmax;
+  RowStage stage;
 };
 
 struct TileCounters {
@@ -526,7 +610,8 @@ struct TileCounters {
 // Phases (1)-(4) for tets [base, base + kTile) of one mesh.  All threads of the block
 // call it; it begins and ends with the block in step.
 template <bool STRICT, bool CULL>
-__device__ __forceinline__ void process_tile(const Params &p, long long base, TileSmem &sm, TileCounters &ctr) {
+__device__ __forceinline__ void process_tile(const Params &p, long long base, long long end, TileSmem &sm,
+                                             TileCounters &ctr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // (1) classification and span counts of this thread's kPerThread consecutive tets
   uint32_t cnt[kPerThread];
@@ -537,7 +622,7 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, Ti
   for (int k = 0; k < kPerThread; ++k) {
     const long long t = base + (long long)tid * kPerThread + k;
     work[k] = 0.f;
-    cnt[k] = t < p.n_tets ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide, work[k]) : 0u;
+    cnt[k] = t < end ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide, work[k]) : 0u;
     if (cnt[k]) {
       work[k] /= (float)cnt[k];  // per span
       wlo = fminf(wlo, work[k]);
@@ -642,11 +727,11 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, Ti
     int dummy = 0;
     load_tet(p, t, V, dummy);
     tet_box(V, p.sh, p.res, bx);
-    const int S = slices_per_span(p, bx.nb);
+    const int S = slices_per_span(p, bx.nb, bx.nc);
     const int c0 = (int)(sp - sm.off[a]) * S;
-    ctr.rows += run_span<STRICT, CULL>(p, t, c0, min(c0 + S, bx.nc), sm.slice_tab);
+    ctr.rows += run_span<STRICT, CULL>(p, t, V, bx, c0, min(c0 + S, bx.nc), sm.slice_tab, sm.stage);
   }
-  __syncthreads();
+  flush_stage(p, sm.stage);
 }
 
 // Adds a block's counters to a mesh's header: one atomic per warp and counter.
@@ -675,12 +760,18 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
   __shared__ TileSmem sm;
   __shared__ unsigned long long tile_s;
   TileCounters ctr;
+  if (threadIdx.x == 0) sm.stage.n = 0;
+  // Guided tiles: full tiles first, then quarter tiles for the last stretch (about two
+  // per block), so that blocks finish close together at the end of the kernel.
+  const long long big = p.big_tiles;
   for (;;) {
     if (threadIdx.x == 0) tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
     __syncthreads();
-    const long long base = (long long)tile_s * kTile;
+    const long long tile = (long long)tile_s;
+    const long long base = tile < big ? tile * kTile : big * kTile + (tile - big) * kSmallTile;
     if (base >= p.n_tets) break;
-    process_tile<STRICT, CULL>(p, base, sm, ctr);
+    const long long end = min(p.n_tets, base + (tile < big ? kTile : kSmallTile));
+    process_tile<STRICT, CULL>(p, base, end, sm, ctr);
   }
   flush_counters(p.hdr, ctr);
 }
@@ -882,6 +973,7 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
   const int n = bh->n_jobs;
   const unsigned long long total = bh->total_tiles;
   int cur = -1;
+  if (threadIdx.x == 0) sm.stage.n = 0;
   for (;;) {
     if (threadIdx.x == 0) {
       tile_s = atomicAdd(&bh->tile_counter, 1ull);
@@ -899,8 +991,9 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
       cur = j;
     }
     const long long base = (long long)(tile_s - tile_base[j]) * kTile;
-    if (sp.cull) process_tile<STRICT, true>(sp, base, sm, ctr);
-    else process_tile<STRICT, false>(sp, base, sm, ctr);
+    const long long end = min(sp.n_tets, base + kTile);
+    if (sp.cull) process_tile<STRICT, true>(sp, base, end, sm, ctr);
+    else process_tile<STRICT, false>(sp, base, end, sm, ctr);
   }
   if (cur >= 0) flush_counters(sp.hdr, ctr);
 }
@@ -1083,10 +1176,12 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     p.sh = kLatticeBits - k;
     p.span_rows = o.span_rows > 0 ? o.span_rows : default_span_rows(res);
     p.exact_all = o.use_filter ? 0 : 1;
-    const long long tiles = (n_tets + kTile - 1) / kTile;
     const bool cull = o.row_cull == 1 || (o.row_cull == 0 && res >= kCullMinRes);
     const int variant = (o.mode == 1 ? 2 : 0) | (cull ? 1 : 0);
     long long grid = (long long)dev->sms * (dev->occ[variant] > 0 ? dev->occ[variant] : 1);
+    const long long tail = 2 * grid * kSmallTile;
+    p.big_tiles = n_tets > tail ? (n_tets - tail) / kTile : 0;
+    const long long tiles = p.big_tiles + (n_tets - p.big_tiles * kTile + kSmallTile - 1) / kSmallTile;
     if (grid > tiles) grid = tiles;
     if (o.profile && profile_begin(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
     voxelize_kernel(variant)<<<(unsigned)grid, kBlock, 0, stream>>>(p);
