@@ -98,6 +98,28 @@ def recorded_traffic(workload: str):
         return None
 
 
+# Algorithmic ALU work per unit (mid-points of the per-unit estimates of the design
+# survey): 25 lane-ops per candidate x-row (four affine bounds, their rounding and
+# certification, the word mask) and 150 per tetrahedron (box, orientation, face data).
+ALU_OPS_PER_ROW = 25
+ALU_OPS_PER_TET = 150
+
+
+def alu_roofline(rows: int, tets: int, kernel_ms: float) -> dict:
+    """The main kernel against the FP32/INT32 lane throughput (152 SMs x 128 lanes x
+    the maximum SM clock), the bound that actually limits it."""
+    mhz = 2070.0
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    peak = 152 * 128 * mhz * 1e6 / 1e12
+    ops = ALU_OPS_PER_ROW * rows + ALU_OPS_PER_TET * tets
+    achieved = ops / (kernel_ms / 1000.0) / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s", "frac": achieved / peak,
+            "algorithmic_ops": ops, "ops_per_row": ALU_OPS_PER_ROW, "ops_per_tet": ALU_OPS_PER_TET}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -469,6 +491,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": recorded_traffic(args.workload), "kernel": "k_voxelize", "kernel_ms": kmean,
                      "algorithmic_bytes": alg_bytes, "peak_source": peak_kind},
+        "alu_roofline": alu_roofline(int(stats["rows"]), n_t, kmean),
         "stats": {"rows": int(stats["rows"]), "spans": int(stats["spans"]),
                   "fallback_rows": int(stats["fallback_rows"]), "degenerate_tets": int(stats["degenerate_tets"]),
                   "wide_tets": int(stats["wide_tets"])},

@@ -46,7 +46,7 @@
 namespace voxtet {
 
 #ifndef VOXTET_MIN_BLOCKS
-#define VOXTET_MIN_BLOCKS 2  // resident blocks per SM the register budget is sized for
+#define VOXTET_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for
 #endif
 
 constexpr int kBlock = 256;             // threads per block
