@@ -569,10 +569,10 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
       else lo = fmaxf(lo, -v);
     }
     const bool live = !amb && lo <= hi;
-    // lo, hi are integral floats in [0, na - 1] when live; clamp so that the word
-    // arithmetic below stays inside the row when not
-    const int x0 = bx.i0 + small_float_to_int(fminf(fmaxf(lo, 0.f), fhi0));
-    const int x1 = bx.i0 + small_float_to_int(fminf(fmaxf(hi, 0.f), fhi0));
+    // lo, hi are integral floats in [0, na - 1] when live; when not, the word indices
+    // below are meaningless but every access through them is predicated off
+    const int x0 = bx.i0 + small_float_to_int(lo);
+    const int x1 = bx.i0 + small_float_to_int(hi);
     or_span_lanes(row, x0, x1, live);
     if (amb) queue_row_staged(p, stage, t, b, c0 + (int)(tab[m_tab - 1][tid] & 15u));
     ++b;
