@@ -14,8 +14,11 @@ Two independent oracles live here:
   (orientation-normalised barycentric signs), for tiny inputs.
 
 Status codes: 0 ok, -1 bad argument, -2 resolution not a power of two in
-[1, 2^19], -3 vertex index out of range, -4 snapped coordinate beyond 2^21,
--5 non-finite vertex coordinate.
+[1, 2^19] (general grids: a side outside [1, 2^19]), -3 vertex index out of
+range, -4 snapped coordinate beyond 2^21, -5 non-finite vertex coordinate.
+
+General grids (``*_grid`` functions) take res = (rx, ry, rz) of any sizes and a
+z-slab [z0, z1); the lattice step per voxel is 2^(20-K), K = ceil(log2(max side)).
 """
 from __future__ import annotations
 
@@ -66,6 +69,14 @@ def _load():
             lib.voxtet_oracle_voxelize.restype = ctypes.c_int
             lib.voxtet_oracle_all_pairs.argtypes = [P, i64, P, i64, i32, i32, P]
             lib.voxtet_oracle_all_pairs.restype = ctypes.c_int
+            lib.voxtet_oracle_snap_grid.argtypes = [P, i64, P, f32, P, P]
+            lib.voxtet_oracle_snap_grid.restype = ctypes.c_int
+            lib.voxtet_oracle_voxelize_grid_fixed.argtypes = [P, i64, P, i64, P, i32, i32, i32, i32, P, P]
+            lib.voxtet_oracle_voxelize_grid_fixed.restype = ctypes.c_int
+            lib.voxtet_oracle_voxelize_grid.argtypes = [P, i64, P, i64, P, f32, P, i32, i32, i32, i32, P, P]
+            lib.voxtet_oracle_voxelize_grid.restype = ctypes.c_int
+            lib.voxtet_oracle_all_pairs_grid.argtypes = [P, i64, P, i64, P, i32, P]
+            lib.voxtet_oracle_all_pairs_grid.restype = ctypes.c_int
             lib.voxtet_oracle_theorem1_dets.argtypes = [P, P, P, P, P, P]
             lib.voxtet_oracle_theorem1_dets.restype = None
             lib.voxtet_oracle_num_threads.argtypes = []
@@ -169,6 +180,102 @@ def all_pairs(xyz: np.ndarray, tets: np.ndarray, res: int, mode: int = 0) -> np.
     if st != OK:
         raise OracleError(st)
     return out.reshape(res, res, W)
+
+
+def _res3(res) -> np.ndarray:
+    r = np.ascontiguousarray(np.asarray(res, dtype=np.int32).reshape(3))
+    return r
+
+
+def grid_exponent(res) -> int:
+    """K = ceil(log2(max side)) of a general grid: the lattice step is 2^(20-K) per voxel."""
+    m = int(max(int(x) for x in res))
+    return (m - 1).bit_length()
+
+
+def snap_grid(verts: np.ndarray, origin, voxel_size: float, res) -> Tuple[int, np.ndarray]:
+    """Lattice coordinates of float vertices on the lattice of the general grid ``res`` = (rx, ry, rz)."""
+    lib = _load()
+    v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+    o = np.ascontiguousarray(np.asarray(origin, dtype=np.float32).reshape(3))
+    out = np.zeros((len(v), 3), dtype=np.int32)
+    st = lib.voxtet_oracle_snap_grid(_ptr(v), len(v), _ptr(o), float(voxel_size), _ptr(_res3(res)), _ptr(out))
+    return st, out
+
+
+def _grid_out(res, z0, z1):
+    rx, ry, rz = (int(x) for x in res)
+    z1 = rz if z1 is None else int(z1)
+    W = (rx + 31) // 32
+    n = max(z1 - int(z0), 0) * ry * W
+    return np.zeros(max(n, 1), dtype=np.uint32), (max(z1 - int(z0), 0), ry, W), z1
+
+
+def voxelize_grid_fixed(xyz: np.ndarray, tets: np.ndarray, res, z0: int = 0, z1: Optional[int] = None,
+                        mode: int = 0, n_threads: int = 0, with_stats: bool = False):
+    """Slices z0 <= l < z1 (default: all) of the general grid res = (rx, ry, rz): uint32 [z1 - z0, ry, W]."""
+    lib = _load()
+    x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    out, shape, z1 = _grid_out(res, z0, z1)
+    stats = np.zeros(3, dtype=np.int64)
+    st = lib.voxtet_oracle_voxelize_grid_fixed(_ptr(x), len(x), _ptr(t), len(t), _ptr(_res3(res)), int(mode),
+                                               int(n_threads), int(z0), int(z1), _ptr(out), _ptr(stats))
+    if st != OK:
+        raise OracleError(st)
+    grid = out[: int(np.prod(shape))].reshape(shape)
+    if with_stats:
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+    return grid
+
+
+def voxelize_grid(verts: np.ndarray, tets: np.ndarray, origin, voxel_size: float, res, z0: int = 0,
+                  z1: Optional[int] = None, mode: int = 0, n_threads: int = 0, with_stats: bool = False):
+    """General-grid voxelization of float32 vertices (snap_grid, then voxelize_grid_fixed)."""
+    lib = _load()
+    v = np.ascontiguousarray(verts, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    o = np.ascontiguousarray(np.asarray(origin, dtype=np.float32).reshape(3))
+    out, shape, z1 = _grid_out(res, z0, z1)
+    stats = np.zeros(3, dtype=np.int64)
+    st = lib.voxtet_oracle_voxelize_grid(_ptr(v), len(v), _ptr(t), len(t), _ptr(o), float(voxel_size),
+                                         _ptr(_res3(res)), int(mode), int(n_threads), int(z0), int(z1), _ptr(out),
+                                         _ptr(stats))
+    if st != OK:
+        raise OracleError(st)
+    grid = out[: int(np.prod(shape))].reshape(shape)
+    if with_stats:
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+    return grid
+
+
+def all_pairs_grid(xyz: np.ndarray, tets: np.ndarray, res, mode: int = 0) -> np.ndarray:
+    """Every sample of the general grid against every tet (no pruning): uint32 [rz, ry, W]."""
+    lib = _load()
+    x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    out, shape, _ = _grid_out(res, 0, None)
+    st = lib.voxtet_oracle_all_pairs_grid(_ptr(x), len(x), _ptr(t), len(t), _ptr(_res3(res)), int(mode),
+                                          _ptr(out))
+    if st != OK:
+        raise OracleError(st)
+    return out[: int(np.prod(shape))].reshape(shape)
+
+
+def unpack_grid(grid: np.ndarray, rx: int) -> np.ndarray:
+    """Bit grid (uint32 [nz, ry, W]) -> bool [nz, ry, rx] (z, y, x)."""
+    g = np.ascontiguousarray(grid, dtype=np.uint32)
+    bits = np.unpackbits(g.view(np.uint8), axis=-1, bitorder="little")
+    return bits[..., :rx].astype(bool)
+
+
+def pack_grid(occ: np.ndarray) -> np.ndarray:
+    """Inverse of ``unpack_grid``: bool [nz, ry, rx] -> uint32 [nz, ry, ceil(rx / 32)]."""
+    nz, ry, rx = occ.shape
+    W = (rx + 31) // 32
+    pad = np.zeros((nz, ry, W * 32), dtype=np.uint8)
+    pad[..., :rx] = occ
+    return np.packbits(pad, axis=-1, bitorder="little").view(np.uint32).reshape(nz, ry, W)
 
 
 def theorem1_dets(A, B, C, D, P) -> Tuple[int, int, int, int]:

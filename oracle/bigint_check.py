@@ -35,8 +35,25 @@ def log2_res(res: int) -> int:
     return res.bit_length() - 1
 
 
+def grid_exponent_py(res: Sequence[int]) -> int:
+    """Smallest K with 2^K >= every side of the grid (sides in [1, 2^19])."""
+    if any(int(r) < 1 or int(r) > (1 << 19) for r in res):
+        raise ValueError("grid sides must be in [1, 2^19]")
+    K = 0
+    while (1 << K) < max(int(r) for r in res):
+        K += 1
+    return K
+
+
 def snap_py(verts: np.ndarray, origin: Sequence[float], h: float, res: int) -> np.ndarray:
-    k = log2_res(res)
+    return _snap_k(verts, origin, h, log2_res(res))
+
+
+def snap_grid_py(verts: np.ndarray, origin: Sequence[float], h: float, res: Sequence[int]) -> np.ndarray:
+    return _snap_k(verts, origin, h, grid_exponent_py(res))
+
+
+def _snap_k(verts: np.ndarray, origin: Sequence[float], h: float, k: int) -> np.ndarray:
     scale = float(2 ** (LATTICE_BITS - k))
     out = np.zeros((len(verts), 3), dtype=np.int64)
     for v in range(len(verts)):
@@ -62,9 +79,17 @@ def orient(A, B, C, D) -> int:
 
 def voxelize_py(xyz: np.ndarray, tets: np.ndarray, res: int, mode: int = 0) -> np.ndarray:
     """Boolean occupancy [l, j, i] (z, y, x) of the union of closed tets."""
-    k = log2_res(res)
+    log2_res(res)
+    return voxelize_grid_py(xyz, tets, (res, res, res), mode)
+
+
+def voxelize_grid_py(xyz: np.ndarray, tets: np.ndarray, res: Sequence[int], mode: int = 0) -> np.ndarray:
+    """Boolean occupancy [l, j, i] of a general grid res = (rx, ry, rz)."""
+    k = grid_exponent_py(res)
     s = 1 << (19 - k)
-    occ = np.zeros((res, res, res), dtype=bool)
+    rx, ry, rz = (int(r) for r in res)
+    occ = np.zeros((rz, ry, rx), dtype=bool)
+    lim = (rx, ry, rz)
     P3 = [[int(c) for c in row] for row in np.asarray(xyz).reshape(-1, 3)]
     for tet in np.asarray(tets).reshape(-1, 4):
         V = [P3[int(i)] for i in tet]
@@ -78,7 +103,7 @@ def voxelize_py(xyz: np.ndarray, tets: np.ndarray, res: int, mode: int = 0) -> n
             mn = min(v[q] for v in V)
             mx = max(v[q] for v in V)
             lo.append(max(0, -((-(mn - s)) // (2 * s))))
-            hi.append(min(res - 1, (mx - s) // (2 * s)))
+            hi.append(min(lim[q] - 1, (mx - s) // (2 * s)))
         for l in range(lo[2], hi[2] + 1):
             for j in range(lo[1], hi[1] + 1):
                 for i in range(lo[0], hi[0] + 1):

@@ -34,6 +34,15 @@
  *
  * Output layout: bit (i, j, l) is word (l*res + j)*W + (i >> 5), bit (i & 31),
  * W = ceil(res / 32); padding bits are zero.
+ *
+ * General grids (the *_grid functions): res = (rx, ry, rz) voxels of the same
+ * edge h, any sizes in [1, 2^19].  The lattice keeps voxel centres on lattice
+ * points: K = ceil(log2(max(rx, ry, rz))), the lattice step is 2^(20-K) per
+ * voxel (so the grid's longest side spans at most 2^20 lattice units) and
+ * X = round_half_even(((double)v - o) / h * 2^(20-K)); samples sit at
+ * (2i+1)s with s = 2^(19-K).  For rx = ry = rz = 2^k this is the cubic grid
+ * above.  Bit (i, j, l) is word ((l - z0)*ry + j)*W + (i >> 5) with
+ * W = ceil(rx / 32), for the slab of slices z0 <= l < z1 that a call produces.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -62,6 +71,18 @@ static int log2_res(int32_t res) {
     int k = 0;
     while ((1 << k) != res) ++k;
     return k;
+}
+
+/* K = ceil(log2(max(res))) of a general grid, or -1 if a side is outside [1, 2^19]. */
+static int grid_exponent(const int32_t res[3]) {
+    int32_t mx = 0;
+    for (int q = 0; q < 3; ++q) {
+        if (res[q] < 1 || res[q] > (1 << 19)) return -1;
+        if (res[q] > mx) mx = res[q];
+    }
+    int K = 0;
+    while (((int32_t)1 << K) < mx) ++K;
+    return K;
 }
 
 /* floor(a / b) for b > 0, without relying on the sign convention of '/'. */
@@ -114,10 +135,8 @@ static int theorem1_inside(const int64_t A[3], const int64_t B[3], const int64_t
 
 /* ------------------------------------------------------------------ snap */
 
-int voxtet_oracle_snap(const float *verts, int64_t n_verts, const float origin[3], float voxel_size,
-                       int32_t res, int32_t *xyz) {
-    int k = log2_res(res);
-    if (k < 0) return OR_ERR_RES;
+static int snap_k(const float *verts, int64_t n_verts, const float origin[3], float voxel_size, int k,
+                  int32_t *xyz) {
     if (n_verts < 0 || !(voxel_size > 0.0f) || !isfinite(voxel_size)) return OR_ERR_ARG;
     for (int q = 0; q < 3; ++q)
         if (!isfinite(origin[q])) return OR_ERR_ARG;
@@ -147,6 +166,20 @@ int voxtet_oracle_snap(const float *verts, int64_t n_verts, const float origin[3
     return status;
 }
 
+int voxtet_oracle_snap(const float *verts, int64_t n_verts, const float origin[3], float voxel_size,
+                       int32_t res, int32_t *xyz) {
+    int k = log2_res(res);
+    if (k < 0) return OR_ERR_RES;
+    return snap_k(verts, n_verts, origin, voxel_size, k, xyz);
+}
+
+int voxtet_oracle_snap_grid(const float *verts, int64_t n_verts, const float origin[3], float voxel_size,
+                            const int32_t res[3], int32_t *xyz) {
+    int K = grid_exponent(res);
+    if (K < 0) return OR_ERR_RES;
+    return snap_k(verts, n_verts, origin, voxel_size, K, xyz);
+}
+
 /* ------------------------------------------------------------------ voxelize */
 
 typedef struct {
@@ -169,7 +202,7 @@ static void load_vertex(const int32_t *xyz, int32_t idx, int64_t out[3]) {
 }
 
 /* Bounding box of a tet in sample indices: samples (2i+1)s with min <= (2i+1)s <= max. */
-static void sample_box(const int64_t V[4][3], int64_t s, int32_t res, tet_box *b) {
+static void sample_box(const int64_t V[4][3], int64_t s, const int32_t res[3], tet_box *b) {
     for (int q = 0; q < 3; ++q) {
         int64_t mn = V[0][q], mx = V[0][q];
         for (int m = 1; m < 4; ++m) {
@@ -179,13 +212,13 @@ static void sample_box(const int64_t V[4][3], int64_t s, int32_t res, tet_box *b
         int64_t lo = ceil_div(mn - s, 2 * s);
         int64_t hi = floor_div(mx - s, 2 * s);
         if (lo < 0) lo = 0;
-        if (hi > res - 1) hi = res - 1;
+        if (hi > res[q] - 1) hi = res[q] - 1;
         b->lo[q] = (int32_t)lo;
         b->hi[q] = (int32_t)hi;
     }
 }
 
-static void prepare(const int32_t *xyz, const int32_t *tets, int64_t n_tets, int32_t res, int64_t s,
+static void prepare(const int32_t *xyz, const int32_t *tets, int64_t n_tets, const int32_t res[3], int64_t s,
                     int mode, tet_box *boxes, int64_t *n_degenerate) {
     int64_t degenerate = 0;
 #pragma omp parallel for schedule(static) reduction(+ : degenerate)
@@ -207,21 +240,19 @@ static void prepare(const int32_t *xyz, const int32_t *tets, int64_t n_tets, int
 
 /* Samples are visited per tet over its bounding box (the paper's loop order),
  * with the grid split into z-chunks so that each thread owns whole words.
- * Only slices z0 <= l < z1 are produced; out_bits holds (z1 - z0)*res*W words
- * (slice z0 first).  The full grid is z0 = 0, z1 = res. */
-int voxtet_oracle_voxelize_fixed_slab(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
-                                      int32_t res, int32_t mode, int32_t n_threads, int32_t z0, int32_t z1,
-                                      uint32_t *out_bits,
-                                      int64_t *stats /* [3]: degenerate tets, samples tested, bits set */) {
-    int k = log2_res(res);
-    if (k < 0) return OR_ERR_RES;
+ * Only slices z0 <= l < z1 are produced; out_bits holds (z1 - z0)*ry*W words
+ * (slice z0 first).  k is the lattice exponent (sample step 2^(20-k)). */
+static int voxelize_core(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
+                         const int32_t res[3], int k, int32_t mode, int32_t n_threads, int32_t z0, int32_t z1,
+                         uint32_t *out_bits, int64_t *stats) {
     if (n_verts < 0 || n_tets < 0 || (mode != 0 && mode != 1)) return OR_ERR_ARG;
-    if (z0 < 0 || z1 > res || z0 > z1) return OR_ERR_ARG;
+    if (z0 < 0 || z1 > res[2] || z0 > z1) return OR_ERR_ARG;
     int st = validate(xyz, n_verts, tets, n_tets);
     if (st != OR_OK) return st;
     const int64_t s = (int64_t)1 << (19 - k);
-    const int64_t W = (res + 31) / 32;
-    const int64_t n_words = (int64_t)(z1 - z0) * res * W;
+    const int64_t ry = res[1];
+    const int64_t W = (res[0] + 31) / 32;
+    const int64_t n_words = (int64_t)(z1 - z0) * ry * W;
     memset(out_bits, 0, (size_t)(n_words > 0 ? n_words : 0) * sizeof(uint32_t));
 #ifdef _OPENMP
     if (n_threads > 0) omp_set_num_threads(n_threads);
@@ -255,7 +286,7 @@ int voxtet_oracle_voxelize_fixed_slab(const int32_t *xyz, int64_t n_verts, const
                         int64_t P[3] = {(2 * i + 1) * s, (2 * j + 1) * s, (2 * l + 1) * s};
                         tested += 1;
                         if (theorem1_inside(V[0], V[1], V[2], V[3], P, mode == 1))
-                            out_bits[((l - z0) * res + j) * W + (i >> 5)] |= (uint32_t)1u << (i & 31);
+                            out_bits[((l - z0) * ry + j) * W + (i >> 5)] |= (uint32_t)1u << (i & 31);
                     }
         }
     }
@@ -268,6 +299,42 @@ int voxtet_oracle_voxelize_fixed_slab(const int32_t *xyz, int64_t n_verts, const
         stats[2] = set;
     }
     return OR_OK;
+}
+
+/* Cubic grid of res = 2^k voxels per axis, slices z0 <= l < z1 (full grid: 0, res). */
+int voxtet_oracle_voxelize_fixed_slab(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
+                                      int32_t res, int32_t mode, int32_t n_threads, int32_t z0, int32_t z1,
+                                      uint32_t *out_bits,
+                                      int64_t *stats /* [3]: degenerate tets, samples tested, bits set */) {
+    int k = log2_res(res);
+    if (k < 0) return OR_ERR_RES;
+    const int32_t r3[3] = {res, res, res};
+    return voxelize_core(xyz, n_verts, tets, n_tets, r3, k, mode, n_threads, z0, z1, out_bits, stats);
+}
+
+/* General grid (rx, ry, rz), slices z0 <= l < z1, lattice coordinates on the
+ * grid's lattice (exponent K = ceil(log2(max side))). */
+int voxtet_oracle_voxelize_grid_fixed(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
+                                      const int32_t res[3], int32_t mode, int32_t n_threads, int32_t z0, int32_t z1,
+                                      uint32_t *out_bits, int64_t *stats) {
+    int K = grid_exponent(res);
+    if (K < 0) return OR_ERR_RES;
+    return voxelize_core(xyz, n_verts, tets, n_tets, res, K, mode, n_threads, z0, z1, out_bits, stats);
+}
+
+/* General grid from float vertices: snap_grid, then voxelize_grid_fixed. */
+int voxtet_oracle_voxelize_grid(const float *verts, int64_t n_verts, const int32_t *tets, int64_t n_tets,
+                                const float origin[3], float voxel_size, const int32_t res[3], int32_t mode,
+                                int32_t n_threads, int32_t z0, int32_t z1, uint32_t *out_bits, int64_t *stats) {
+    if (n_verts < 0) return OR_ERR_ARG;
+    int32_t *xyz = (int32_t *)malloc((size_t)(n_verts > 0 ? n_verts : 1) * 3 * sizeof(int32_t));
+    if (!xyz) return OR_ERR_ARG;
+    int st = voxtet_oracle_snap_grid(verts, n_verts, origin, voxel_size, res, xyz);
+    if (st == OR_OK)
+        st = voxtet_oracle_voxelize_grid_fixed(xyz, n_verts, tets, n_tets, res, mode, n_threads, z0, z1, out_bits,
+                                               stats);
+    free(xyz);
+    return st;
 }
 
 int voxtet_oracle_voxelize_fixed(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
@@ -293,31 +360,45 @@ int voxtet_oracle_voxelize(const float *verts, int64_t n_verts, const int32_t *t
 
 /* Every sample against every tet, no bounding-box pruning, one thread.  Used
  * to pin the pruned loop above on tiny inputs. */
-int voxtet_oracle_all_pairs(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
-                            int32_t res, int32_t mode, uint32_t *out_bits) {
-    int k = log2_res(res);
-    if (k < 0) return OR_ERR_RES;
+static int all_pairs_core(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
+                          const int32_t res[3], int k, int32_t mode, uint32_t *out_bits) {
     if (n_verts < 0 || n_tets < 0 || (mode != 0 && mode != 1)) return OR_ERR_ARG;
     int st = validate(xyz, n_verts, tets, n_tets);
     if (st != OR_OK) return st;
     const int64_t s = (int64_t)1 << (19 - k);
-    const int64_t W = (res + 31) / 32;
-    memset(out_bits, 0, (size_t)((int64_t)res * res * W) * sizeof(uint32_t));
-    for (int64_t l = 0; l < res; ++l)
-        for (int64_t j = 0; j < res; ++j)
-            for (int64_t i = 0; i < res; ++i) {
+    const int64_t rx = res[0], ry = res[1], rz = res[2];
+    const int64_t W = (rx + 31) / 32;
+    memset(out_bits, 0, (size_t)(rz * ry * W) * sizeof(uint32_t));
+    for (int64_t l = 0; l < rz; ++l)
+        for (int64_t j = 0; j < ry; ++j)
+            for (int64_t i = 0; i < rx; ++i) {
                 int64_t P[3] = {(2 * i + 1) * s, (2 * j + 1) * s, (2 * l + 1) * s};
                 for (int64_t t = 0; t < n_tets; ++t) {
                     int64_t V[4][3];
                     for (int m = 0; m < 4; ++m) load_vertex(xyz, tets[4 * t + m], V[m]);
                     if (mode == 0 && signed_volume6(V[0], V[1], V[2], V[3]) == 0) continue;
                     if (theorem1_inside(V[0], V[1], V[2], V[3], P, mode == 1)) {
-                        out_bits[(l * res + j) * W + (i >> 5)] |= (uint32_t)1u << (i & 31);
+                        out_bits[(l * ry + j) * W + (i >> 5)] |= (uint32_t)1u << (i & 31);
                         break;
                     }
                 }
             }
     return OR_OK;
+}
+
+int voxtet_oracle_all_pairs(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
+                            int32_t res, int32_t mode, uint32_t *out_bits) {
+    int k = log2_res(res);
+    if (k < 0) return OR_ERR_RES;
+    const int32_t r3[3] = {res, res, res};
+    return all_pairs_core(xyz, n_verts, tets, n_tets, r3, k, mode, out_bits);
+}
+
+int voxtet_oracle_all_pairs_grid(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
+                                 const int32_t res[3], int32_t mode, uint32_t *out_bits) {
+    int K = grid_exponent(res);
+    if (K < 0) return OR_ERR_RES;
+    return all_pairs_core(xyz, n_verts, tets, n_tets, res, K, mode, out_bits);
 }
 
 /* The four determinants of Theorem 1 for one point, as (hi, lo) halves of the
