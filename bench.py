@@ -42,6 +42,9 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-mesh batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) run")
     ap.add_argument("--requests", type=int, default=10000, help="requests in the served run")
+    ap.add_argument("--partition", choices=["replica", "slab"], default="replica",
+                    help="N > 1: a replica of the whole job per rank (weak scaling), or one z-slab of the same "
+                         "grid per rank (strong scaling, no exchange)")
     return ap.parse_args()
 
 
@@ -384,7 +387,16 @@ def run_ours(args):
     verts = torch.from_numpy(cfg["verts"]).to(dev)
     tets = torch.from_numpy(cfg["tets"]).to(dev)
     ws = vt.alloc_workspace(n_t, n_v, res, dev)
-    grid = vt.alloc_grid(res, dev)
+    slab = args.partition == "slab" and world > 1
+    if slab:  # this rank's z-slab of the one grid, cut by the mesh's per-slice tet counts
+        from paper_2106_01326_gb300 import slabs
+
+        w = slabs.slice_weights(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"], res)
+        z_range = slabs.rank_slab(res, rank, world, w)
+        grid = vt.alloc_grid_dims((res, res, res), z_range, dev)
+    else:
+        z_range = (0, res)
+        grid = vt.alloc_grid(res, dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
@@ -397,9 +409,17 @@ def run_ours(args):
         tuned = autotune.tune(verts, tets, cfg["origin"], cfg["voxel_size"], res, reps=3)
         span_rows, row_cull = tuned["span_rows"], tuned["row_cull"]
 
+    def call(v, t, profile=False):
+        if slab:
+            vt.voxelize_grid(v, t, cfg["origin"], cfg["voxel_size"], (res, res, res), z_range=z_range, out=grid,
+                             workspace=ws, sync=False, span_rows=span_rows, row_cull=row_cull, profile=profile,
+                             stream=stream)
+        else:
+            vt.voxelize(v, t, cfg["origin"], cfg["voxel_size"], res, out=grid, workspace=ws, sync=False,
+                        span_rows=span_rows, row_cull=row_cull, profile=profile, stream=stream)
+
     def step():
-        vt.voxelize(verts, tets, cfg["origin"], cfg["voxel_size"], res, out=grid, workspace=ws, sync=False,
-                    span_rows=span_rows, row_cull=row_cull, profile=True, stream=stream)
+        call(verts, tets, profile=True)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -446,8 +466,7 @@ def run_ours(args):
     def e2e_step():
         d_verts.copy_(h_verts, non_blocking=True)
         d_tets.copy_(h_tets, non_blocking=True)
-        vt.voxelize(d_verts, d_tets, cfg["origin"], cfg["voxel_size"], res, out=grid, workspace=ws, sync=False,
-                    span_rows=span_rows, row_cull=row_cull, stream=stream)
+        call(d_verts, d_tets)
         h_grid.copy_(grid, non_blocking=True)
 
     for _ in range(2):
@@ -469,24 +488,28 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    value = whole_job_rate(n_t, world, args.steps, total_ms)
-    gvox = world * (res ** 3) * args.steps / (total_ms / 1000.0) / 1e9
+    jobs = 1 if slab else world  # meshes voxelized per step across all ranks
+    value = whole_job_rate(n_t, jobs, args.steps, total_ms)
+    gvox = jobs * (res ** 3) * args.steps / (total_ms / 1000.0) / 1e9
     kmean = statistics.mean(kern_ms)
-    alg_bytes = 16 * n_t + 12 * n_v + res ** 3 // 8
+    grid_bytes = grid.numel() * 4  # this rank's slab (the whole grid unless partitioned)
+    alg_bytes = 16 * n_t + 12 * n_v + grid_bytes
     peak, peak_kind = load_peaks()
     achieved = alg_bytes / (kmean / 1000.0) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "strong" if slab else "weak",
         "vs_baseline": None, "dtype": "f32+i64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: 60^3 jittered Kuhn lattice, 2% slivers, {n_t} tets, {n_v} verts "
                                f"-> {res}^3 bit grid", "res": res, "n_tets": n_t, "n_verts": n_v,
-                   "l2": "flushed between timed steps (512 MiB write)", "parallelism": f"replicas x{world}",
+                   "l2": "flushed between timed steps (512 MiB write)",
+                   "parallelism": f"z-slabs x{world}" if slab else f"replicas x{world}",
                    "span_rows": span_rows, "row_cull": {0: "auto", 1: "on", 2: "off"}[row_cull],
                    "launch_shape": "autotuned" if tuned else "given"},
         "gvox_per_s": gvox,
-        "e2e": {"value": whole_job_rate(n_t, world, args.steps, e2e_total), "unit": UNIT,
-                "h2d_bytes_per_step": 12 * n_v + 16 * n_t, "d2h_bytes_per_step": res ** 3 // 8},
+        "e2e": {"value": whole_job_rate(n_t, jobs, args.steps, e2e_total), "unit": UNIT,
+                "h2d_bytes_per_step": 12 * n_v + 16 * n_t, "d2h_bytes_per_step": grid_bytes},
         "gpu_launches": int(launches),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": recorded_traffic(args.workload), "kernel": "k_voxelize", "kernel_ms": kmean,

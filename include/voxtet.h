@@ -53,7 +53,8 @@ extern "C" {
 typedef enum {
     VOXTET_OK = 0,
     VOXTET_ERR_ARG = -1,       /* null pointer, negative size, bad option, non-positive voxel_size */
-    VOXTET_ERR_RES = -2,       /* res not a power of two in [1, VOXTET_MAX_RES] */
+    VOXTET_ERR_RES = -2,       /* res not a power of two in [1, VOXTET_MAX_RES] (general grids: a side
+                                  outside [1, VOXTET_MAX_RES]) */
     VOXTET_ERR_INDEX = -3,     /* a tetrahedron names a vertex outside [0, n_verts) (device-detected) */
     VOXTET_ERR_RANGE = -4,     /* a snapped coordinate exceeds 2^21 in magnitude (device-detected) */
     VOXTET_ERR_NAN = -5,       /* a vertex coordinate is NaN or infinite (device-detected) */
@@ -123,6 +124,31 @@ int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, 
 int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
                         int32_t res, uint32_t *d_out_bits, void *d_workspace, size_t ws_bytes,
                         const voxtet_opts *opts, void *stream);
+
+/* The same operation on a general grid, or on a z-slab of one (the paper fixes
+ * no grid; its voxelization loop of Section 3 is unchanged by the grid's shape).
+ *   res          HOST int32[3]: voxels along x, y, z, each in [1, VOXTET_MAX_RES],
+ *                any values (not only powers of two, not necessarily equal)
+ *   z_begin, z_end  the slices z_begin <= l < z_end are produced,
+ *                0 <= z_begin <= z_end <= res[2]; (0, res[2]) is the whole grid
+ *   d_out_bits   DEVICE uint32 [(z_end - z_begin) * res[1] * W], W = ceil(res[0] / 32):
+ *                bit (i, j, l) is word ((l - z_begin) * res[1] + j) * W + (i >> 5),
+ *                bit i & 31; padding bits are zero.  May be NULL only when the
+ *                slab is empty (z_begin == z_end), which writes nothing.
+ * The lattice keeps voxel centres on lattice points: with K = ceil(log2(max side))
+ * a voxel spans 2^(20-K) lattice units (so the longest side spans at most 2^20),
+ * X = round_half_even(((double)v - o) / h * 2^(20-K)) and |X| <= 2^21 is required.
+ * A cubic 2^k grid gives exactly voxelize_tets's grid; a grid whose longest side
+ * lies in (2^(k-1), 2^k] is the [0:rz, 0:ry, 0:rx] block of the 2^k grid with the
+ * same origin and voxel size, and slabs of one grid concatenate to the whole grid,
+ * so ranks that each produce one slab need no exchange.  Other arguments and the
+ * workspace are as for voxelize_tets (voxtet_workspace_size with any valid res).
+ * Returns VOXTET_ERR_RES for a side outside [1, VOXTET_MAX_RES] and VOXTET_ERR_ARG
+ * for a slab outside [0, res[2]] or res == NULL. */
+int voxelize_tets_grid(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                       const float grid_origin[3], float voxel_size, const int32_t res[3], int32_t z_begin,
+                       int32_t z_end, uint32_t *d_out_bits, void *d_workspace, size_t ws_bytes,
+                       const voxtet_opts *opts, void *stream);
 
 /* Synchronize `stream` and return the device-detected status the last call on
  * this workspace recorded (VOXTET_OK if none). */

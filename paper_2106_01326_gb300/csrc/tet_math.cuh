@@ -50,14 +50,16 @@ struct Box {
 };
 
 // Sample-index box of one axis: samples (2i+1)s with mn <= (2i+1)s <= mx, clamped to
-// [0, res-1].  sh = 20 - k, so 2s = 1 << sh and s = 1 << (sh - 1); arithmetic shifts
-// give floor division for negative operands.
-__device__ __forceinline__ void axis_box(int mn, int mx, int sh, int res, int &lo, int &n) {
+// [lo_lim, hi_lim] (the grid's samples on that axis, or a z-slab of them).  The
+// lattice step is 2s = 1 << sh per voxel (sh = 20 - K, K = ceil(log2 of the grid's
+// longest side)) and s = 1 << (sh - 1); arithmetic shifts give floor division for
+// negative operands.
+__device__ __forceinline__ void axis_box(int mn, int mx, int sh, int lo_lim, int hi_lim, int &lo, int &n) {
   const int s = 1 << (sh - 1);
   int a = (mn + s - 1) >> sh;  // ceil((mn - s) / 2s)
   int b = (mx - s) >> sh;      // floor((mx - s) / 2s)
-  a = a < 0 ? 0 : a;
-  b = b > res - 1 ? res - 1 : b;
+  a = a < lo_lim ? lo_lim : a;
+  b = b > hi_lim ? hi_lim : b;
   lo = a;
   n = b - a + 1;
 }
@@ -65,14 +67,15 @@ __device__ __forceinline__ void axis_box(int mn, int mx, int sh, int res, int &l
 __device__ __forceinline__ int imin4(int a, int b, int c, int d) { return min(min(a, b), min(c, d)); }
 __device__ __forceinline__ int imax4(int a, int b, int c, int d) { return max(max(a, b), max(c, d)); }
 
-// Bounding box of the samples of an (oriented or not) tet; returns the extent E.
-__device__ __forceinline__ int tet_box(const int3 V[4], int sh, int res, Box &bx) {
+// Bounding box of the samples of an (oriented or not) tet within a grid of rx x ry
+// samples per slice and slices z0 <= l < z1; returns the extent E.
+__device__ __forceinline__ int tet_box(const int3 V[4], int sh, int rx, int ry, int z0, int z1, Box &bx) {
   int mnx = imin4(V[0].x, V[1].x, V[2].x, V[3].x), mxx = imax4(V[0].x, V[1].x, V[2].x, V[3].x);
   int mny = imin4(V[0].y, V[1].y, V[2].y, V[3].y), mxy = imax4(V[0].y, V[1].y, V[2].y, V[3].y);
   int mnz = imin4(V[0].z, V[1].z, V[2].z, V[3].z), mxz = imax4(V[0].z, V[1].z, V[2].z, V[3].z);
-  axis_box(mnx, mxx, sh, res, bx.i0, bx.na);
-  axis_box(mny, mxy, sh, res, bx.j0, bx.nb);
-  axis_box(mnz, mxz, sh, res, bx.l0, bx.nc);
+  axis_box(mnx, mxx, sh, 0, rx - 1, bx.i0, bx.na);
+  axis_box(mny, mxy, sh, 0, ry - 1, bx.j0, bx.nb);
+  axis_box(mnz, mxz, sh, z0, z1 - 1, bx.l0, bx.nc);
   return max(max(mxx - mnx, mxy - mny), mxz - mnz);
 }
 

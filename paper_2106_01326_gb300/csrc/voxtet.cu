@@ -88,9 +88,10 @@ struct Params {
   RowItem *rowq;    // [q_cap]
   uint32_t *redo;   // [ceil(n_tets / 32)] bitmap
   unsigned q_cap;
-  int res;
-  int W;
-  int sh;           // 20 - log2(res)
+  int rx, ry;       // samples per row and rows per slice
+  int z0, z1;       // slices z0 <= l < z1 are produced; out holds (z1 - z0) * ry * W words
+  int W;            // words per row, ceil(rx / 32)
+  int sh;           // log2 of the lattice step per voxel, 20 - ceil(log2(longest side))
   int span_rows;    // target bounding-box rows per span
   int exact_all;    // 1: every tet goes to the exact kernel
   int cull;         // 1: skip rows outside each slice's cross-section (batched kernel)
@@ -225,7 +226,7 @@ __device__ __forceinline__ bool load_tet(const Params &p, long long t, int3 V[4]
 __device__ __forceinline__ int oriented_tet(const Params &p, long long t, int3 V[4], Box &bx) {
   int dummy = 0;
   load_tet(p, t, V, dummy);
-  const int E = tet_box(V, p.sh, p.res, bx);
+  const int E = tet_box(V, p.sh, p.rx, p.ry, p.z0, p.z1, bx);
   if (v6_sign(V, E) < 0) {
     const int3 tmp = V[2];
     V[2] = V[3];
@@ -251,7 +252,7 @@ __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, i
   int3 V[4];
   if (!load_tet(p, t, V, err)) return 0;
   Box bx;
-  const int E = tet_box(V, p.sh, p.res, bx);
+  const int E = tet_box(V, p.sh, p.rx, p.ry, p.z0, p.z1, bx);
   if (v6_sign(V, E) == 0) {
     ++n_degenerate;
     return 0;
@@ -546,7 +547,7 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
       const float cf = (float)(c0 + k);
 #pragma unroll
       for (int m = 0; m < 4; ++m) ac[m] = __fmaf_rn(ga[m], cf, al[m]);
-      row = p.out + ((size_t)(bx.l0 + c0 + k) * p.res + (bx.j0 + b)) * p.W;
+      row = p.out + ((size_t)(bx.l0 - p.z0 + c0 + k) * p.ry + (bx.j0 + b)) * p.W;
     }
     float lo = 0.f, hi = fhi0;
     bool amb = false;
@@ -726,7 +727,7 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
     Box bx;
     int dummy = 0;
     load_tet(p, t, V, dummy);
-    tet_box(V, p.sh, p.res, bx);
+    tet_box(V, p.sh, p.rx, p.ry, p.z0, p.z1, bx);
     const int S = slices_per_span(p, bx.nb, bx.nc);
     const int c0 = (int)(sp - sm.off[a]) * S;
     ctr.rows += run_span<STRICT, CULL>(p, t, V, bx, c0, min(c0 + S, bx.nc), sm.slice_tab, sm.stage);
@@ -792,7 +793,7 @@ __device__ __forceinline__ void exact_tet_rows(const Params &p, const int3 V[4],
     const int c = (int)(r / (unsigned)bx.nb), b = (int)(r - (unsigned)c * bx.nb);
     int lo, hi;
     if (exact_row<STRICT, T>(X, nup, nlo, bx.na, b, c, lo, hi)) {
-      uint32_t *row = p.out + ((size_t)(bx.l0 + c) * p.res + (bx.j0 + b)) * p.W;
+      uint32_t *row = p.out + ((size_t)(bx.l0 - p.z0 + c) * p.ry + (bx.j0 + b)) * p.W;
       or_span(row, bx.i0 + lo, bx.i0 + hi);
     }
   }
@@ -828,7 +829,7 @@ __device__ __forceinline__ void exact_job(const Params &p) {
     permute_slots<i64>(X, slot);
     int lo, hi;
     if (exact_row<STRICT, i64>(X, nup, nlo, bx.na, it.b, it.c, lo, hi)) {
-      uint32_t *row = p.out + ((size_t)(bx.l0 + it.c) * p.res + (bx.j0 + it.b)) * p.W;
+      uint32_t *row = p.out + ((size_t)(bx.l0 - p.z0 + it.c) * p.ry + (bx.j0 + it.b)) * p.W;
       or_span(row, bx.i0 + lo, bx.i0 + hi);
     }
   }
@@ -1092,6 +1093,32 @@ static int log2_res(int res) {
   return k;
 }
 
+// The grid of one call: rx x ry x rz voxels, slices z0 <= l < z1 produced, lattice
+// exponent K (the lattice step is 2^(20-K) per voxel, K = ceil(log2 of the longest side)).
+struct GridDims {
+  int rx, ry, rz, z0, z1, K;
+  int longest() const { return rx > ry ? (rx > rz ? rx : rz) : (ry > rz ? ry : rz); }
+  long long out_words() const { return (long long)(z1 - z0) * ry * ((rx + 31) / 32); }
+};
+
+static GridDims cubic_dims(int res, int k) { return GridDims{res, res, res, 0, res, k}; }
+
+// General grid from the caller's sides and slab; VOXTET_ERR_RES for a side outside
+// [1, VOXTET_MAX_RES], VOXTET_ERR_ARG for a slab outside [0, rz].
+static int general_dims(const int32_t res[3], int32_t z_begin, int32_t z_end, GridDims &g) {
+  for (int q = 0; q < 3; ++q)
+    if (res[q] < 1 || res[q] > VOXTET_MAX_RES) return VOXTET_ERR_RES;
+  g.rx = res[0];
+  g.ry = res[1];
+  g.rz = res[2];
+  if (z_begin < 0 || z_end > g.rz || z_begin > z_end) return VOXTET_ERR_ARG;
+  g.z0 = z_begin;
+  g.z1 = z_end;
+  g.K = 0;
+  while ((1 << g.K) < g.longest()) ++g.K;
+  return VOXTET_OK;
+}
+
 static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 // Carved workspace: header, snapped vertices, tet queue, row queue, redo bitmap.
@@ -1155,8 +1182,8 @@ static int check_opts(const voxtet_opts &o) {
 }
 
 // Shared tail of both entry points: vertices are already in the workspace.
-static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *tets, long long n_tets, int res, int k,
-                        uint32_t *out, const voxtet_opts &o, cudaStream_t stream) {
+static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *tets, long long n_tets,
+                        const GridDims &g, uint32_t *out, const voxtet_opts &o, cudaStream_t stream) {
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   if (n_tets > 0) {
@@ -1171,12 +1198,15 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     p.rowq = w.rowq;
     p.redo = w.redo;
     p.q_cap = w.q_cap;
-    p.res = res;
-    p.W = (res + 31) / 32;
-    p.sh = kLatticeBits - k;
-    p.span_rows = o.span_rows > 0 ? o.span_rows : default_span_rows(res);
+    p.rx = g.rx;
+    p.ry = g.ry;
+    p.z0 = g.z0;
+    p.z1 = g.z1;
+    p.W = (g.rx + 31) / 32;
+    p.sh = kLatticeBits - g.K;
+    p.span_rows = o.span_rows > 0 ? o.span_rows : default_span_rows(g.longest());
     p.exact_all = o.use_filter ? 0 : 1;
-    const bool cull = o.row_cull == 1 || (o.row_cull == 0 && res >= kCullMinRes);
+    const bool cull = o.row_cull == 1 || (o.row_cull == 0 && g.longest() >= kCullMinRes);
     const int variant = (o.mode == 1 ? 2 : 0) | (cull ? 1 : 0);
     long long grid = (long long)dev->sms * (dev->occ[variant] > 0 ? dev->occ[variant] : 1);
     const long long tail = 2 * grid * kSmallTile;
@@ -1226,18 +1256,53 @@ static int grid_blocks(long long n, int per_block, int sms) {
   return (int)(b < 1 ? 1 : b);
 }
 
+// Sizes, alignment and workspace capacity shared by every single-mesh entry point.
+static int buffer_checks(long long n_verts, const void *tets, long long n_tets, const uint32_t *out, void *ws,
+                         size_t ws_bytes, bool out_may_be_null = false) {
+  if (n_verts < 0 || n_tets < 0 || n_verts > 0x7FFFFFFFLL || n_tets > 0xFFFFFFFFLL) return VOXTET_ERR_ARG;
+  if (!out && !out_may_be_null) return VOXTET_ERR_ARG;
+  if (n_tets > 0 && (!tets || (reinterpret_cast<uintptr_t>(tets) & 15))) return VOXTET_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(out) & 3) return VOXTET_ERR_ARG;
+  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return VOXTET_ERR_WORKSPACE;
+  if (ws_bytes < workspace_bytes(n_tets, n_verts, nullptr, nullptr)) return VOXTET_ERR_WORKSPACE;
+  return VOXTET_OK;
+}
+
 static int common_checks(long long n_verts, const void *tets, long long n_tets, int res, const uint32_t *out,
                          void *ws, size_t ws_bytes, const voxtet_opts &o, int &k) {
   int st = check_opts(o);
   if (st != VOXTET_OK) return st;
   k = log2_res(res);
   if (k < 0) return VOXTET_ERR_RES;
-  if (n_verts < 0 || n_tets < 0 || n_verts > 0x7FFFFFFFLL || n_tets > 0xFFFFFFFFLL) return VOXTET_ERR_ARG;
-  if (!out) return VOXTET_ERR_ARG;
-  if (n_tets > 0 && (!tets || (reinterpret_cast<uintptr_t>(tets) & 15))) return VOXTET_ERR_ARG;
-  if (reinterpret_cast<uintptr_t>(out) & 3) return VOXTET_ERR_ARG;
-  if (!ws || (reinterpret_cast<uintptr_t>(ws) & 255)) return VOXTET_ERR_WORKSPACE;
-  if (ws_bytes < voxtet_workspace_size(n_tets, n_verts, res)) return VOXTET_ERR_WORKSPACE;
+  return buffer_checks(n_verts, tets, n_tets, out, ws, ws_bytes);
+}
+
+// Snap kernel launch: X = round_half_even(((double)v - o) / h * 2^(20-K)).
+static int launch_snap(const Workspace &w, const float *d_verts, long long n_verts, const float grid_origin[3],
+                       float voxel_size, int K, cudaStream_t stream) {
+  DeviceInfo *dev = nullptr;
+  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+  if (n_verts <= 0) return VOXTET_OK;
+  const double h = (double)voxel_size;
+  const double scale = std::ldexp(1.0, kLatticeBits - K);
+  int e2 = 0;
+  const double mant = std::frexp(h, &e2);
+  const int use_mul = mant == 0.5 ? 1 : 0;
+  const double mul = use_mul ? std::ldexp(1.0, kLatticeBits - K - (e2 - 1)) : 0.0;
+  k_snap<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(
+      d_verts, n_verts, (double)grid_origin[0], (double)grid_origin[1], (double)grid_origin[2], h, scale, mul,
+      use_mul, w.verts4, w.hdr);
+  g_launches.fetch_add(1);
+  return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
+}
+
+static int float_input_checks(const float *d_verts, long long n_verts, const float grid_origin[3],
+                              float voxel_size) {
+  if (!grid_origin) return VOXTET_ERR_ARG;
+  if (n_verts > 0 && (!d_verts || (reinterpret_cast<uintptr_t>(d_verts) & 3))) return VOXTET_ERR_ARG;
+  if (!(voxel_size > 0.0f) || !std::isfinite(voxel_size)) return VOXTET_ERR_ARG;
+  for (int q = 0; q < 3; ++q)
+    if (!std::isfinite(grid_origin[q])) return VOXTET_ERR_ARG;
   return VOXTET_OK;
 }
 
@@ -1274,33 +1339,44 @@ int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, 
   int k = 0;
   int st = common_checks(n_verts, d_tets, n_tets, res, d_out_bits, d_workspace, ws_bytes, o, k);
   if (st != VOXTET_OK) return st;
-  if (!grid_origin) return VOXTET_ERR_ARG;
-  if (n_verts > 0 && (!d_verts || (reinterpret_cast<uintptr_t>(d_verts) & 3))) return VOXTET_ERR_ARG;
-  if (!(voxel_size > 0.0f) || !std::isfinite(voxel_size)) return VOXTET_ERR_ARG;
-  for (int q = 0; q < 3; ++q)
-    if (!std::isfinite(grid_origin[q])) return VOXTET_ERR_ARG;
+  st = float_input_checks(d_verts, n_verts, grid_origin, voxel_size);
+  if (st != VOXTET_OK) return st;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   Workspace w;
   workspace_bytes(n_tets, n_verts, &w, d_workspace);
-  const long long W = (res + 31) / 32;
-  st = launch_prologue(w, d_out_bits, (long long)res * res * W, o.accumulate ? 0 : 1, stream);
+  const GridDims g = cubic_dims(res, k);
+  st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
   if (st != VOXTET_OK) return st;
-  DeviceInfo *dev = nullptr;
-  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
-  if (n_verts > 0) {
-    const double h = (double)voxel_size;
-    const double scale = std::ldexp(1.0, kLatticeBits - k);
-    int e2 = 0;
-    const double mant = std::frexp(h, &e2);
-    const int use_mul = mant == 0.5 ? 1 : 0;
-    const double mul = use_mul ? std::ldexp(1.0, kLatticeBits - k - (e2 - 1)) : 0.0;
-    k_snap<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(
-        d_verts, n_verts, (double)grid_origin[0], (double)grid_origin[1], (double)grid_origin[2], h, scale, mul,
-        use_mul, w.verts4, w.hdr);
-    g_launches.fetch_add(1);
-    if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
-  }
-  return run_voxelize(w, n_verts, d_tets, n_tets, res, k, d_out_bits, o, stream);
+  st = launch_snap(w, d_verts, n_verts, grid_origin, voxel_size, g.K, stream);
+  if (st != VOXTET_OK) return st;
+  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream);
+}
+
+int voxelize_tets_grid(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                       const float grid_origin[3], float voxel_size, const int32_t res[3], int32_t z_begin,
+                       int32_t z_end, uint32_t *d_out_bits, void *d_workspace, size_t ws_bytes,
+                       const voxtet_opts *opts, void *stream_) {
+  voxtet_opts o;
+  resolve_opts(opts, o);
+  int st = check_opts(o);
+  if (st != VOXTET_OK) return st;
+  if (!res) return VOXTET_ERR_ARG;
+  GridDims g;
+  st = general_dims(res, z_begin, z_end, g);
+  if (st != VOXTET_OK) return st;
+  // an empty slab writes nothing, so its output pointer may be NULL
+  st = buffer_checks(n_verts, d_tets, n_tets, d_out_bits, d_workspace, ws_bytes, g.out_words() == 0);
+  if (st != VOXTET_OK) return st;
+  st = float_input_checks(d_verts, n_verts, grid_origin, voxel_size);
+  if (st != VOXTET_OK) return st;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  Workspace w;
+  workspace_bytes(n_tets, n_verts, &w, d_workspace);
+  st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
+  if (st != VOXTET_OK) return st;
+  st = launch_snap(w, d_verts, n_verts, grid_origin, voxel_size, g.K, stream);
+  if (st != VOXTET_OK) return st;
+  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream);
 }
 
 int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_tets, int64_t n_tets, int32_t res,
@@ -1315,8 +1391,8 @@ int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   Workspace w;
   workspace_bytes(n_tets, n_verts, &w, d_workspace);
-  const long long W = (res + 31) / 32;
-  st = launch_prologue(w, d_out_bits, (long long)res * res * W, o.accumulate ? 0 : 1, stream);
+  const GridDims g = cubic_dims(res, k);
+  st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
   if (st != VOXTET_OK) return st;
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
@@ -1325,7 +1401,7 @@ int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
   }
-  return run_voxelize(w, n_verts, d_tets, n_tets, res, k, d_out_bits, o, stream);
+  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream);
 }
 
 int voxtet_last_status(const void *d_workspace, void *stream_) {
@@ -1364,7 +1440,7 @@ const char *voxtet_strerror(int s) {
   switch (s) {
     case VOXTET_OK: return "ok";
     case VOXTET_ERR_ARG: return "invalid argument";
-    case VOXTET_ERR_RES: return "resolution must be a power of two in [1, VOXTET_MAX_RES]";
+    case VOXTET_ERR_RES: return "resolution must be a power of two in [1, VOXTET_MAX_RES] (grid sides: in [1, VOXTET_MAX_RES])";
     case VOXTET_ERR_INDEX: return "tetrahedron vertex index out of range";
     case VOXTET_ERR_RANGE: return "snapped vertex coordinate beyond 2^21 lattice units";
     case VOXTET_ERR_NAN: return "non-finite vertex coordinate";
@@ -1470,7 +1546,10 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
     d.p.rowq = w.rowq;
     d.p.redo = w.redo;
     d.p.q_cap = w.q_cap;
-    d.p.res = res;
+    d.p.rx = res;
+    d.p.ry = res;
+    d.p.z0 = 0;
+    d.p.z1 = res;
     d.p.W = (res + 31) / 32;
     d.p.sh = kLatticeBits - k;
     d.p.span_rows = J.span_rows > 0 ? J.span_rows : (o.span_rows > 0 ? o.span_rows : default_span_rows(res));

@@ -10,7 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
-from typing import Optional, Sequence
+from typing import Optional, Sequence, Tuple
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libvoxtet.so")
@@ -22,7 +22,7 @@ MAX_RES = 8192
 
 # every symbol include/voxtet.h declares
 EXPORTED = (
-    "voxtet_default_opts", "voxtet_workspace_size", "voxelize_tets", "voxelize_tets_fixed",
+    "voxtet_default_opts", "voxtet_workspace_size", "voxelize_tets", "voxelize_tets_fixed", "voxelize_tets_grid",
     "voxtet_last_status", "voxtet_read_stats", "voxtet_strerror", "voxtet_launch_count",
     "voxelize_tets_noalloc", "voxtet_batch_workspace_size", "voxelize_tets_batched", "voxtet_plan_create",
     "voxtet_plan_run", "voxtet_plan_query", "voxtet_plan_wait", "voxtet_plan_destroy",
@@ -78,6 +78,10 @@ def load(path: Optional[str] = None):
                                       ctypes.POINTER(Opts), P]
         lib.voxelize_tets.restype = ctypes.c_int
         lib.voxelize_tets_fixed.argtypes = [P, i64, P, i64, i32, P, P, sz, ctypes.POINTER(Opts), P]
+        lib.voxelize_tets_fixed.restype = ctypes.c_int
+        lib.voxelize_tets_grid.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, ctypes.POINTER(i32 * 3),
+                                           i32, i32, P, P, sz, ctypes.POINTER(Opts), P]
+        lib.voxelize_tets_grid.restype = ctypes.c_int
         lib.voxelize_tets_fixed.restype = ctypes.c_int
         lib.voxtet_last_status.argtypes = [P, P]
         lib.voxtet_last_status.restype = ctypes.c_int
@@ -219,6 +223,45 @@ def voxelize_fixed(xyz, tets, res: int, out=None, workspace=None, mode: int = 0,
     o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull)
     st = lib.voxelize_tets_fixed(xyz.data_ptr(), n_v, tets.data_ptr(), n_t, int(res), out.data_ptr(),
                                  workspace.data_ptr(), workspace.numel(), ctypes.byref(o), _stream_ptr(stream))
+    if raise_on_error:
+        if st != OK:
+            raise VoxtetError(st)
+        return out
+    return st, out
+
+
+def alloc_grid_dims(res3: Sequence[int], z_range: Optional[Tuple[int, int]] = None, device=None):
+    """Buffer for a general grid or slab: int32 [z_end - z_begin, ry, ceil(rx / 32)]."""
+    torch = _torch()
+    rx, ry, rz = (int(x) for x in res3)
+    z0, z1 = (0, rz) if z_range is None else (int(z_range[0]), int(z_range[1]))
+    return torch.empty((max(z1 - z0, 0), ry, (rx + 31) // 32), dtype=torch.int32, device=device or "cuda")
+
+
+def voxelize_grid(verts, tets, origin: Sequence[float], voxel_size: float, res3: Sequence[int],
+                  z_range: Optional[Tuple[int, int]] = None, out=None, workspace=None, mode: int = 0,
+                  accumulate: bool = False, use_filter: bool = True, sync: bool = True, span_rows: int = 0,
+                  stream=None, raise_on_error: bool = True, profile: bool = False, row_cull: int = 0):
+    """General grid res3 = (rx, ry, rz), any sides in [1, MAX_RES], or its z-slab
+    ``z_range`` = (z_begin, z_end): int32 tensor [z_end - z_begin, ry, ceil(rx / 32)]."""
+    torch = _torch()
+    lib = load()
+    _check_cuda_tensor(verts, "verts", torch.float32)
+    _check_cuda_tensor(tets, "tets", torch.int32)
+    n_v, n_t = verts.shape[0], tets.shape[0]
+    rx, ry, rz = (int(x) for x in res3)
+    z0, z1 = (0, rz) if z_range is None else (int(z_range[0]), int(z_range[1]))
+    if out is None:
+        out = alloc_grid_dims(res3, (z0, z1), verts.device)  # an empty slab passes a NULL pointer
+    _check_cuda_tensor(out, "out", torch.int32)
+    if workspace is None:
+        workspace = alloc_workspace(n_t, n_v, 1, verts.device)
+    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull)
+    org = (ctypes.c_float * 3)(*[float(x) for x in origin])
+    r3 = (ctypes.c_int32 * 3)(rx, ry, rz)
+    st = lib.voxelize_tets_grid(verts.data_ptr(), n_v, tets.data_ptr(), n_t, ctypes.byref(org), float(voxel_size),
+                                ctypes.byref(r3), z0, z1, out.data_ptr(), workspace.data_ptr(), workspace.numel(),
+                                ctypes.byref(o), _stream_ptr(stream))
     if raise_on_error:
         if st != OK:
             raise VoxtetError(st)

@@ -77,3 +77,29 @@ def test_argument_checks_before_launch(lib):
     bad = vt.make_opts(block=96)
     assert call(opts=bad) == vt.ERR_ARG
     assert lib.voxelize_tets_fixed(P, 4, P, 1, 7, P, P, ws, ctypes.byref(o), None) == vt.ERR_RES
+
+
+def test_grid_argument_checks_before_launch(lib):
+    """voxelize_tets_grid rejects bad sides, slabs and buffers on the host."""
+    P = 1 << 20
+    o = vt.make_opts()
+    org = (ctypes.c_float * 3)(0.0, 0.0, 0.0)
+    ws = vt.workspace_size(1, 4, 8)
+
+    def call(res=(5, 7, 9), z0=0, z1=9, h=0.1, out=P, work=P, wsb=ws, res_ptr=True):
+        r3 = (ctypes.c_int32 * 3)(*res)
+        rp = ctypes.byref(r3) if res_ptr else None
+        return lib.voxelize_tets_grid(P, 4, P, 1, ctypes.byref(org), h, rp, z0, z1, out, work, wsb,
+                                      ctypes.byref(o), None)
+
+    assert call(res=(0, 7, 9)) == vt.ERR_RES
+    assert call(res=(5, vt.MAX_RES + 1, 9)) == vt.ERR_RES
+    assert call(res=(5, 7, -3), z1=0) == vt.ERR_RES
+    assert call(z0=-1) == vt.ERR_ARG
+    assert call(z0=5, z1=4) == vt.ERR_ARG
+    assert call(z1=10) == vt.ERR_ARG
+    assert call(res_ptr=False) == vt.ERR_ARG
+    assert call(out=0) == vt.ERR_ARG
+    assert call(z0=3, z1=3, out=0, h=-1.0) == vt.ERR_ARG  # NULL output allowed for an empty slab only
+    assert call(h=-1.0) == vt.ERR_ARG
+    assert call(wsb=ws - 1) == vt.ERR_WORKSPACE

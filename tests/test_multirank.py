@@ -53,3 +53,62 @@ def test_single_rank_needs_no_process_group():
 
     assert bench.max_over_ranks(5.0) == 5.0
     assert bench.whole_job_rate(10, 1, 2, 1000.0) == 20.0
+
+
+def _slab_rank_main(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2106_01326_gb300 import meshgen as mg
+    from paper_2106_01326_gb300 import slabs
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    v, t = mg.clipped_kuhn_lattice(10, 0.25, 21, mg.torus_sdf(0.3, 0.12))
+    res3, h = (40, 36, 44), 1.0 / 44
+    w = slabs.slice_weights(v, t, (0, 0, 0), h, res3[2])
+    z0, z1 = slabs.rank_slab(res3[2], rank, world, w)
+    mine = oracle.voxelize_grid(v, t, (0, 0, 0), h, res3, z0=z0, z1=z1)
+    got = [None] * world
+    dist.all_gather_object(got, (z0, z1, mine))
+    dist.destroy_process_group()
+    full = oracle.voxelize_grid(v, t, (0, 0, 0), h, res3)
+    cat = np.concatenate([g for _, _, g in sorted(got, key=lambda x: x[0])], axis=0)
+    q.put((rank, (z0, z1), bool((cat == full).all()), [c[:2] for c in got]))
+
+
+def test_two_gloo_ranks_slabs_concatenate_to_grid():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_rank_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=180) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(ok for _, _, ok, _ in out)
+    (a0, a1), (b0, b1) = out[0][1], out[1][1]
+    assert a0 == 0 and a1 == b0 and b1 == 44 and 0 < a1 < 44
+
+
+def test_slab_cuts_cover_and_balance():
+    sys.path.insert(0, ROOT)
+    import numpy as np
+
+    from paper_2106_01326_gb300 import slabs
+
+    assert slabs.slab_cuts(10, 3) == [(0, 4), (4, 7), (7, 10)]
+    assert slabs.slab_cuts(2, 4) == [(0, 1), (1, 2), (2, 2), (2, 2)]
+    assert slabs.slab_cuts(0, 2) == [(0, 0), (0, 0)]
+    w = np.zeros(100)
+    w[60:80] = 1.0  # all the work in slices 60..79
+    cuts = slabs.slab_cuts(100, 4, w)
+    assert cuts[0][0] == 0 and cuts[-1][1] == 100
+    assert all(a[1] == b[0] for a, b in zip(cuts, cuts[1:]))
+    shares = [w[a:b].sum() for a, b in cuts]
+    assert max(shares) == 5.0 and min(shares) == 5.0
+    with pytest.raises(ValueError):
+        slabs.slab_cuts(5, 0)
