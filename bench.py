@@ -201,6 +201,34 @@ def cpu_oracle_sample(cfg, slab, n_threads=0):
     return value, dt, (z1 - z0), oracle.num_threads() if n_threads <= 0 else n_threads
 
 
+def paper_cpu_comparison(cfg):
+    """The paper's CPU method in float and double (oracle/paper_cpu.c) on the same snapped mesh:
+    whole-grid mismatches against the exact oracle, per-test sign disagreements on the middle
+    128 slices, and the same on a tie-heavy soup (faces on planes through samples)."""
+    import oracle
+    from paper_2106_01326_gb300 import meshgen as mg
+
+    res = cfg["res"]
+    st, xyz = oracle.snap(cfg["verts"], cfg["origin"], cfg["voxel_size"], res)
+    assert st == 0
+    out = {"what": "Theorem 1 in binary floating point on the oracle's snapped inputs (not exact)"}
+    t0 = time.perf_counter()
+    exact = oracle.voxelize_fixed(xyz, cfg["tets"], res)
+    out["exact_oracle_s"] = time.perf_counter() - t0
+    for prec in ("float", "double"):
+        t0 = time.perf_counter()
+        g = oracle.paper_cpu(xyz, cfg["tets"], res, prec, 0)
+        out[f"{prec}_s"] = time.perf_counter() - t0
+        extra, missing = oracle.mismatches(g, exact)
+        out[f"{prec}_grid_mismatches"] = {"extra": extra, "missing": missing}
+    z0 = max(0, res // 2 - 64)
+    out["per_test_disagreements_middle_128_slices"] = oracle.paper_cpu_disagreements(xyz, cfg["tets"], res, z0,
+                                                                                     min(res, z0 + 128))
+    sx, stt = mg.coplanar_face_soup(400, 64, seed=124, spread=60)
+    out["per_test_disagreements_coplanar_soup_64"] = oracle.paper_cpu_disagreements(sx, stt, 64)
+    return out
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -531,7 +559,8 @@ def run_ours(args):
         v, dt, depth, cores = cpu_oracle_sample(cfg, args.slab)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"z-slab of {depth} of {res} slices, all tets overlapping it, {dt:.2f} s; "
-                                          f"tets/s = n_tets x {depth}/{res} / time"}
+                                          f"tets/s = n_tets x {depth}/{res} / time",
+                                "paper_cpu_method": paper_cpu_comparison(cfg)}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

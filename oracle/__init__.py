@@ -13,6 +13,9 @@ Two independent oracles live here:
 * ``bigint_check`` -- pure Python integers, a different formulation
   (orientation-normalised barycentric signs), for tiny inputs.
 
+``paper_cpu.c`` (same library) is not an oracle: it is the paper's CPU method in
+float or double, kept here to count what inexact arithmetic decides differently.
+
 Status codes: 0 ok, -1 bad argument, -2 resolution not a power of two in
 [1, 2^19] (general grids: a side outside [1, 2^19]), -3 vertex index out of
 range, -4 snapped coordinate beyond 2^21, -5 non-finite vertex coordinate.
@@ -32,6 +35,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "voxtet_oracle.c")
+_SRC_PAPER = os.path.join(_HERE, "paper_cpu.c")
 _LIB_PATH = os.path.join(_HERE, "libvoxtet_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -41,11 +45,12 @@ OK, ERR_ARG, ERR_RES, ERR_INDEX, ERR_RANGE, ERR_NAN = 0, -1, -2, -3, -4, -5
 
 def build(force: bool = False) -> str:
     """Compile the C oracle with gcc (OpenMP, no FP contraction)."""
-    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_PAPER))
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, "-lm"]
+           "-fno-fast-math", "-Wall", "-o", tmp, _SRC, _SRC_PAPER, "-lm"]
     subprocess.run(cmd, check=True, cwd=_HERE)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -77,6 +82,10 @@ def _load():
             lib.voxtet_oracle_voxelize_grid.restype = ctypes.c_int
             lib.voxtet_oracle_all_pairs_grid.argtypes = [P, i64, P, i64, P, i32, P]
             lib.voxtet_oracle_all_pairs_grid.restype = ctypes.c_int
+            lib.voxtet_paper_cpu.argtypes = [P, i64, P, i64, i32, i32, i32, i32, P]
+            lib.voxtet_paper_cpu.restype = ctypes.c_int
+            lib.voxtet_paper_cpu_disagreements.argtypes = [P, i64, P, i64, i32, i32, i32, i32, P]
+            lib.voxtet_paper_cpu_disagreements.restype = ctypes.c_int
             lib.voxtet_oracle_theorem1_dets.argtypes = [P, P, P, P, P, P]
             lib.voxtet_oracle_theorem1_dets.restype = None
             lib.voxtet_oracle_num_threads.argtypes = []
@@ -276,6 +285,47 @@ def pack_grid(occ: np.ndarray) -> np.ndarray:
     pad = np.zeros((nz, ry, W * 32), dtype=np.uint8)
     pad[..., :rx] = occ
     return np.packbits(pad, axis=-1, bitorder="little").view(np.uint32).reshape(nz, ry, W)
+
+
+def paper_cpu(xyz: np.ndarray, tets: np.ndarray, res: int, precision: str = "float", mode: int = 0,
+              n_threads: int = 0) -> np.ndarray:
+    """The paper's CPU method in float or double (paper_cpu.c): NOT exact, for counting its
+    differences from ``voxelize_fixed``.  Same inputs and grid layout."""
+    lib = _load()
+    x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    W = (res + 31) // 32
+    out = np.zeros(res * res * W, dtype=np.uint32)
+    st = lib.voxtet_paper_cpu(_ptr(x), len(x), _ptr(t), len(t), int(res), {"float": 0, "double": 1}[precision],
+                              int(mode), int(n_threads), _ptr(out))
+    if st != OK:
+        raise OracleError(st)
+    return out.reshape(res, res, W)
+
+
+def paper_cpu_disagreements(xyz: np.ndarray, tets: np.ndarray, res: int, z0: int = 0, z1: Optional[int] = None,
+                            n_threads: int = 0) -> dict:
+    """Per-test sign-pattern disagreements of Theorem 1 in float / double with exact integers
+    over every (tet, sample in its box) pair in slices [z0, z1)."""
+    lib = _load()
+    x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
+    c = np.zeros(6, dtype=np.int64)
+    st = lib.voxtet_paper_cpu_disagreements(_ptr(x), len(x), _ptr(t), len(t), int(res), int(z0),
+                                            int(res if z1 is None else z1), int(n_threads), _ptr(c))
+    if st != OK:
+        raise OracleError(st)
+    keys = ("tests", "exact_closed_inside", "float_closed", "float_strict", "double_closed", "double_strict")
+    return {k: int(v) for k, v in zip(keys, c)}
+
+
+def mismatches(a: np.ndarray, b: np.ndarray) -> Tuple[int, int]:
+    """(samples set in a only, samples set in b only) of two bit grids of the same shape."""
+    x = np.ascontiguousarray(a, dtype=np.uint32)
+    y = np.ascontiguousarray(b, dtype=np.uint32)
+    only_a = np.unpackbits((x & ~y).view(np.uint8)).sum()
+    only_b = np.unpackbits((y & ~x).view(np.uint8)).sum()
+    return int(only_a), int(only_b)
 
 
 def theorem1_dets(A, B, C, D, P) -> Tuple[int, int, int, int]:

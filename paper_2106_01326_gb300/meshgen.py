@@ -236,6 +236,53 @@ def add_slivers(
 
 # ---------------------------------------------------------------- single-mesh workloads
 
+def coplanar_face_soup(n_tets: int, res: int, seed: int, spread: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Tie-heavy tet soup on the lattice of a cubic 2^k grid (int32 lattice coordinates, tets).
+
+    Each tet has one face on a plane n . X = n . P through a voxel-centre sample P
+    ((2a+1)s per axis, s = 2^(19-k)) with a small integer normal n; that plane holds
+    many other samples, so the four orientation values of many samples are exactly
+    zero.  The face's three vertices and the fourth vertex lie within ``spread``
+    voxels of P at unaligned lattice points, so the zeros only appear after
+    cancellation of large products -- the case where inexact arithmetic picks signs
+    at random.  All coordinates stay within 2^21.
+    """
+    k = res.bit_length() - 1
+    if res < 1 or (1 << k) != res:
+        raise ValueError("res must be a power of two")
+    s = 1 << (19 - k)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    verts: List[np.ndarray] = []
+    tets: List[List[int]] = []
+    lim = 1 << 21
+    while len(tets) < n_tets:
+        P = (2 * rng.integers(0, res, size=3) + 1) * s
+        nrm = rng.integers(-3, 4, size=3)
+        if not nrm.any():
+            continue
+        c = int(nrm @ P)
+        ax = int(np.argmax(np.abs(nrm)))
+        face: List[np.ndarray] = []
+        for _ in range(50):
+            q = P + rng.integers(-spread * s, spread * s + 1, size=3)
+            r = c - int(nrm @ q) + int(nrm[ax]) * int(q[ax])
+            if r % int(nrm[ax]):
+                continue
+            q[ax] = r // int(nrm[ax])
+            if np.abs(q).max() > lim:
+                continue
+            face.append(q)
+            if len(face) == 3:
+                break
+        U = P + rng.integers(-spread * s, spread * s + 1, size=3)
+        if len(face) < 3 or np.abs(U).max() > lim:
+            continue
+        b = len(verts)
+        verts += face + [U]
+        tets.append([b, b + 1, b + 2, b + 3])
+    return np.asarray(verts, dtype=np.int32).reshape(-1, 3), np.asarray(tets, dtype=np.int32).reshape(-1, 4)
+
+
 def single_mesh_config(name: str) -> dict:
     """The single-mesh workloads, by name.
 

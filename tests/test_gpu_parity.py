@@ -114,6 +114,18 @@ def test_unjittered_lattice_ties(vt, res):
             assert_same(got, ref, res, f"lattice N={N} off={off} mode={mode}")
 
 
+@pytest.mark.parametrize("res,spread,n", [(64, 60, 400), (256, 30, 2000), (256, 200, 150), (1024, 400, 40)])
+def test_coplanar_face_ties(vt, res, spread, n):
+    """Faces on planes through many samples, vertices at unaligned lattice points: exact zeros
+    that only appear after cancellation (float and double both get some of these wrong)."""
+    xyz, tets = mg.coplanar_face_soup(n, res, seed=res + spread, spread=spread)
+    for mode in (0, 1):
+        ref = oracle.voxelize_fixed(xyz, tets, res, mode=mode)
+        for use_filter in (True, False):
+            got = gpu_fixed(vt, xyz, tets, res, mode=mode, use_filter=use_filter)
+            assert (got == ref).all(), (mode, use_filter)
+
+
 def test_wide_tets_128bit_path(vt):
     """Tets wider than 2^20 lattice units take the 128-bit exact path."""
     rng = np.random.default_rng(7)
