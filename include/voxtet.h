@@ -150,6 +150,43 @@ int voxelize_tets_grid(const float *d_verts, int64_t n_verts, const int32_t *d_t
                        int32_t z_end, uint32_t *d_out_bits, void *d_workspace, size_t ws_bytes,
                        const voxtet_opts *opts, void *stream);
 
+/* ------------------------------------------------------------------ sparse output
+ *
+ * Brick-sparse grids (Section 5, "Octrees", notes that voxel data is usually
+ * stored sparsely).  The grid is a general grid as in voxelize_tets_grid (same
+ * lattice, same samples, same bits) with sides up to VOXTET_SPARSE_MAX_SIDE, cut
+ * into bricks of 32 x 8 x 8 voxels (x, y, z).  Only bricks holding a set voxel are
+ * returned: brick (bx, by, bz) covers voxels 32bx <= i < 32bx + 32, 8by <= j <
+ * 8by + 8, 8bz <= l < 8bz + 8; its VOXTET_BRICK_WORDS words are word dz * 8 + dy
+ * = bits of voxels (32bx + bit, 8by + dy, 8bz + dz); its key is
+ * bx | by << 16 | bz << 32.  Keys come out in increasing order.  Voxels outside
+ * the grid (a partial last brick) are zero. */
+#define VOXTET_SPARSE_MAX_SIDE 65536
+#define VOXTET_BRICK_WORDS 64
+
+/* Bytes of device scratch voxelize_tets_sparse needs for this grid and slab depth
+ * (256-byte aligned): a dense slab of slab_depth slices plus compaction counters.
+ * 0 if the arguments are invalid. */
+size_t voxtet_sparse_scratch_size(const int32_t res[3], int32_t slab_depth);
+
+/* Voxelize into bricks.  The grid is built slab_depth slices at a time (a multiple
+ * of 8, >= 8) in d_scratch and each slab is compacted; larger slabs mean fewer
+ * passes over the tetrahedra.
+ *   res            HOST int32[3], sides in [1, VOXTET_SPARSE_MAX_SIDE]
+ *   d_brick_keys   DEVICE uint64 [max_bricks], 8-byte aligned
+ *   d_brick_words  DEVICE uint32 [max_bricks][VOXTET_BRICK_WORDS], 4-byte aligned
+ *   n_bricks       HOST out: the number of non-empty bricks, also when it exceeds
+ *                  max_bricks (then VOXTET_ERR_NOMEM is returned and only the first
+ *                  max_bricks bricks are written)
+ *   d_scratch      DEVICE, voxtet_sparse_scratch_size(res, slab_depth) bytes, 256-byte aligned
+ * Other arguments as voxelize_tets; opts->accumulate must be 0.  The call always
+ * synchronizes `stream` (it returns the brick count). */
+int voxelize_tets_sparse(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                         const float grid_origin[3], float voxel_size, const int32_t res[3], int32_t slab_depth,
+                         uint64_t *d_brick_keys, uint32_t *d_brick_words, int64_t max_bricks, int64_t *n_bricks,
+                         void *d_scratch, size_t scratch_bytes, void *d_workspace, size_t ws_bytes,
+                         const voxtet_opts *opts, void *stream);
+
 /* Synchronize `stream` and return the device-detected status the last call on
  * this workspace recorded (VOXTET_OK if none). */
 int voxtet_last_status(const void *d_workspace, void *stream);

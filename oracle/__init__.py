@@ -328,6 +328,37 @@ def mismatches(a: np.ndarray, b: np.ndarray) -> Tuple[int, int]:
     return int(only_a), int(only_b)
 
 
+def dense_to_bricks(grid: np.ndarray, rx: int) -> Tuple[np.ndarray, np.ndarray]:
+    """Non-empty 32 x 8 x 8 bricks of a bit grid uint32 [rz, ry, W]: (keys uint64 [n], words
+    uint32 [n, 64]) in increasing key order, key = bx | by << 16 | bz << 32, word dz * 8 + dy."""
+    g = np.ascontiguousarray(grid, dtype=np.uint32)
+    rz, ry, W = g.shape
+    assert W == (rx + 31) // 32
+    nbz, nby = -(-rz // 8), -(-ry // 8)
+    pad = np.zeros((nbz * 8, nby * 8, W), dtype=np.uint32)
+    pad[:rz, :ry, :] = g
+    b = pad.reshape(nbz, 8, nby, 8, W).transpose(0, 2, 4, 1, 3).reshape(nbz, nby, W, 64)
+    nz = b.any(axis=3)
+    bz, by, bx = np.nonzero(nz)  # row-major order = increasing (bz, by, bx)
+    keys = bx.astype(np.uint64) | (by.astype(np.uint64) << np.uint64(16)) | (bz.astype(np.uint64) << np.uint64(32))
+    return keys, b[nz]
+
+
+def bricks_to_dense(keys: np.ndarray, words: np.ndarray, res) -> np.ndarray:
+    """Inverse of ``dense_to_bricks`` for a general grid res = (rx, ry, rz)."""
+    rx, ry, rz = (int(x) for x in res)
+    W = (rx + 31) // 32
+    nbz, nby = -(-rz // 8), -(-ry // 8)
+    b = np.zeros((nbz, nby, W, 64), dtype=np.uint32)
+    k = np.asarray(keys, dtype=np.uint64)
+    bx = (k & np.uint64(0xFFFF)).astype(np.int64)
+    by = ((k >> np.uint64(16)) & np.uint64(0xFFFF)).astype(np.int64)
+    bz = (k >> np.uint64(32)).astype(np.int64)
+    b[bz, by, bx] = np.asarray(words, dtype=np.uint32).reshape(-1, 64)
+    dense = b.reshape(nbz, nby, W, 8, 8).transpose(0, 3, 1, 4, 2).reshape(nbz * 8, nby * 8, W)
+    return np.ascontiguousarray(dense[:rz, :ry, :])
+
+
 def theorem1_dets(A, B, C, D, P) -> Tuple[int, int, int, int]:
     """(D_a, D_b, D_c, D_d) of Theorem 1 as Python ints, from the C oracle."""
     lib = _load()

@@ -55,6 +55,7 @@ constexpr int kBlock = 256;             // threads per block
 // the larger boxes of fine grids better).
 static __host__ __device__ int default_span_rows(int res) { return res >= 1024 ? 128 : 256; }
 constexpr int kCullMinRes = 256;        // automatic row culling from this resolution up
+constexpr int kMaxFilterRows = 8192;    // box rows per slice the fused kernel's slice table can hold
 
 // Workspace header (first 256 bytes of the workspace).
 struct Header {
@@ -260,7 +261,9 @@ __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, i
   if (bx.na <= 0 || bx.nb <= 0 || bx.nc <= 0) return 0;
   const bool wide = E > kNarrowExtent;
   n_wide += wide;
-  if (wide || p.exact_all) {
+  // boxes taller than kMaxFilterRows rows (only in grids wider than 8192, sparse output)
+  // exceed the slice table's 14-bit row fields and go to the exact kernel as well
+  if (wide || p.exact_all || bx.nb > kMaxFilterRows) {
     const unsigned k = atomicAdd(&p.hdr->tetq_count, 1u);  // each tet is queued once: k < n_tets
     p.tetq[k] = (uint32_t)t;
     return 0;
@@ -788,9 +791,9 @@ __device__ __forceinline__ void exact_tet_rows(const Params &p, const int3 V[4],
   int slot[4], nup = 0, nlo = 0;
   slot_order<T>(X, slot, nup, nlo);
   permute_slots<T>(X, slot);
-  const unsigned rows = (unsigned)bx.nb * (unsigned)bx.nc;
-  for (unsigned r = threadIdx.x; r < rows; r += blockDim.x) {
-    const int c = (int)(r / (unsigned)bx.nb), b = (int)(r - (unsigned)c * bx.nb);
+  const unsigned long long rows = (unsigned long long)bx.nb * (unsigned long long)bx.nc;
+  for (unsigned long long r = threadIdx.x; r < rows; r += blockDim.x) {
+    const int c = (int)(r / (unsigned long long)bx.nb), b = (int)(r - (unsigned long long)c * bx.nb);
     int lo, hi;
     if (exact_row<STRICT, T>(X, nup, nlo, bx.na, b, c, lo, hi)) {
       uint32_t *row = p.out + ((size_t)(bx.l0 - p.z0 + c) * p.ry + (bx.j0 + b)) * p.W;
@@ -1825,3 +1828,253 @@ extern "C" int voxelize_tets_noalloc(const float *d_verts, int64_t n_verts, cons
   return voxelize_tets(d_verts, n_verts, d_tets, n_tets, grid_origin, voxel_size, res, d_out_bits, ws,
                        (size_t)VOXTET_NOALLOC_SCRATCH_BYTES, &o, stream);
 }
+
+// ------------------------------------------------------------------ brick-sparse output
+//
+// Section 5 ("Octrees") notes that voxel data is usually stored sparsely.  Here a grid
+// is produced one z-slab at a time into a dense slab buffer (the fused kernels
+// unchanged, on the slab's slices), and the slab is then compacted into bricks of
+// 32 x 8 x 8 voxels: the brick's 64 row-words of the dense layout, word dz * 8 + dy.
+// Three bandwidth-bound kernels per slab: count the non-empty bricks of each block of
+// bricks, scan the block counts (one block, which also advances the running total),
+// and write keys and words of the non-empty bricks in slab order, so the output is
+// sorted by (bz, by, bx).
+
+namespace voxtet {
+
+constexpr int kBrickRows = 8;                        // y rows per brick
+constexpr int kBrickSlices = 8;                      // z slices per brick
+constexpr int kBrickWords = kBrickRows * kBrickSlices;
+constexpr int kCompactBlock = 256;
+
+struct SparseHeader {
+  unsigned long long total;  // non-empty bricks of all slabs so far (may exceed the capacity)
+  int sticky_bits;           // device-detected status bits of every slab
+  int pad;
+  unsigned long long reserved[30];
+};
+static_assert(sizeof(SparseHeader) == 256, "sparse header is 256 bytes");
+
+struct SlabBricks {
+  const uint32_t *dense;  // [nz][ry][W] words of the slab
+  int W, ry, nz;          // words per row, rows per slice, slices in the slab
+  int nby, nbz;           // bricks along y and z in the slab
+  int bz0;                // global brick z of the slab's first slice
+  long long n;            // W * nby * nbz bricks, bx fastest
+};
+
+__device__ __forceinline__ const uint32_t *brick_origin(const SlabBricks &s, long long b, int &bx, int &by, int &bz,
+                                                        int &ny, int &nz) {
+  bx = (int)(b % s.W);
+  const long long t = b / s.W;
+  by = (int)(t % s.nby);
+  bz = (int)(t / s.nby);
+  ny = min(kBrickRows, s.ry - by * kBrickRows);
+  nz = min(kBrickSlices, s.nz - bz * kBrickSlices);
+  return s.dense + ((size_t)bz * kBrickSlices * s.ry + (size_t)by * kBrickRows) * s.W + bx;
+}
+
+// OR of a brick's row-words (rows past the slab's edges are absent).  Consecutive
+// threads take consecutive bx, so every load of a warp is one contiguous run of words.
+__device__ __forceinline__ bool brick_nonempty(const SlabBricks &s, long long b) {
+  int bx, by, bz, ny, nz;
+  const uint32_t *o = brick_origin(s, b, bx, by, bz, ny, nz);
+  uint32_t acc = 0;
+  for (int dz = 0; dz < nz; ++dz)
+    for (int dy = 0; dy < ny; ++dy) acc |= o[((size_t)dz * s.ry + dy) * s.W];
+  return acc != 0;
+}
+
+__global__ void __launch_bounds__(kCompactBlock) k_brick_count(SlabBricks s, unsigned long long *block_counts) {
+  const long long b = (long long)blockIdx.x * kCompactBlock + threadIdx.x;
+  const bool ne = b < s.n && brick_nonempty(s, b);
+  const int c = __syncthreads_count(ne);
+  if (threadIdx.x == 0) block_counts[blockIdx.x] = (unsigned long long)c;
+}
+
+// One block: exclusive scan of the block counts in place, offset by the running total,
+// which then advances; the slab's device-detected status bits join the sticky bits.
+__global__ void __launch_bounds__(1024) k_brick_scan(unsigned long long *counts, long long n_blocks,
+                                                     SparseHeader *sh, const Header *slab_hdr) {
+  __shared__ unsigned long long warp_sums[32];
+  __shared__ unsigned long long carry;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (tid == 0) {
+    carry = sh->total;
+    sh->sticky_bits |= slab_hdr->status_bits;
+  }
+  __syncthreads();
+  for (long long base = 0; base < n_blocks; base += 1024) {
+    const long long i = base + tid;
+    const unsigned long long v = i < n_blocks ? counts[i] : 0ull;
+    unsigned long long x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+      if (lane >= d) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+      unsigned long long w = warp_sums[lane];
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+        if (lane >= d) w += y;
+      }
+      warp_sums[lane] = w;  // inclusive
+    }
+    __syncthreads();
+    const unsigned long long before = carry + (warp ? warp_sums[warp - 1] : 0ull) + x - v;
+    if (i < n_blocks) counts[i] = before;
+    __syncthreads();
+    if (tid == 0) carry += warp_sums[31];
+    __syncthreads();
+  }
+  if (tid == 0) sh->total = carry;
+}
+
+__global__ void __launch_bounds__(kCompactBlock) k_brick_write(SlabBricks s, const unsigned long long *block_offsets,
+                                                               uint64_t *keys, uint32_t *words, long long cap) {
+  __shared__ unsigned warp_base[kCompactBlock / 32];
+  const long long b = (long long)blockIdx.x * kCompactBlock + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const bool ne = b < s.n && brick_nonempty(s, b);
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, ne);
+  if (lane == 0) warp_base[warp] = __popc(m);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned run = 0;
+    for (int w = 0; w < kCompactBlock / 32; ++w) {
+      const unsigned c = warp_base[w];
+      warp_base[w] = run;
+      run += c;
+    }
+  }
+  __syncthreads();
+  if (!ne) return;
+  const unsigned long long slot =
+      block_offsets[blockIdx.x] + warp_base[warp] + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+  if (slot >= (unsigned long long)cap) return;
+  int bx, by, bz, ny, nz;
+  const uint32_t *o = brick_origin(s, b, bx, by, bz, ny, nz);
+  keys[slot] = (uint64_t)bx | ((uint64_t)by << 16) | ((uint64_t)(s.bz0 + bz) << 32);
+  uint32_t *dst = words + slot * kBrickWords;
+  for (int dz = 0; dz < kBrickSlices; ++dz)
+    for (int dy = 0; dy < kBrickRows; ++dy)
+      dst[dz * kBrickRows + dy] = (dz < nz && dy < ny) ? o[((size_t)dz * s.ry + dy) * s.W] : 0u;
+}
+
+// Scratch: header, one dense slab, the per-block counts of a slab's bricks.
+static size_t sparse_scratch_bytes(const GridDims &g, int depth, long long *n_blocks_out) {
+  const long long W = (g.rx + 31) / 32;
+  const long long nby = (g.ry + kBrickRows - 1) / kBrickRows;
+  const long long nbz = (depth + kBrickSlices - 1) / kBrickSlices;
+  const long long n_blocks = (W * nby * nbz + kCompactBlock - 1) / kCompactBlock;
+  if (n_blocks_out) *n_blocks_out = n_blocks;
+  return align256(sizeof(SparseHeader)) + align256((size_t)depth * g.ry * W * 4) +
+         align256((size_t)(n_blocks > 0 ? n_blocks : 1) * 8);
+}
+
+static int sparse_dims(const int32_t res[3], int32_t depth, GridDims &g) {
+  if (!res) return VOXTET_ERR_ARG;
+  for (int q = 0; q < 3; ++q)
+    if (res[q] < 1 || res[q] > VOXTET_SPARSE_MAX_SIDE) return VOXTET_ERR_RES;
+  if (depth < kBrickSlices || depth % kBrickSlices != 0) return VOXTET_ERR_ARG;
+  g.rx = res[0];
+  g.ry = res[1];
+  g.rz = res[2];
+  g.z0 = 0;
+  g.z1 = res[2];
+  g.K = 0;
+  while ((1 << g.K) < g.longest()) ++g.K;
+  return VOXTET_OK;
+}
+
+}  // namespace voxtet
+
+extern "C" {
+
+size_t voxtet_sparse_scratch_size(const int32_t res[3], int32_t slab_depth) {
+  GridDims g;
+  if (sparse_dims(res, slab_depth, g) != VOXTET_OK) return 0;
+  return sparse_scratch_bytes(g, slab_depth, nullptr);
+}
+
+int voxelize_tets_sparse(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
+                         const float grid_origin[3], float voxel_size, const int32_t res[3], int32_t slab_depth,
+                         uint64_t *d_brick_keys, uint32_t *d_brick_words, int64_t max_bricks, int64_t *n_bricks,
+                         void *d_scratch, size_t scratch_bytes, void *d_workspace, size_t ws_bytes,
+                         const voxtet_opts *opts, void *stream_) {
+  voxtet_opts o;
+  resolve_opts(opts, o);
+  int st = check_opts(o);
+  if (st != VOXTET_OK) return st;
+  if (o.accumulate) return VOXTET_ERR_ARG;
+  GridDims g;
+  st = sparse_dims(res, slab_depth, g);
+  if (st != VOXTET_OK) return st;
+  if (!n_bricks || max_bricks < 0) return VOXTET_ERR_ARG;
+  if (max_bricks > 0 && (!d_brick_keys || !d_brick_words || (reinterpret_cast<uintptr_t>(d_brick_keys) & 7) ||
+                         (reinterpret_cast<uintptr_t>(d_brick_words) & 3)))
+    return VOXTET_ERR_ARG;
+  long long n_blocks = 0;
+  if (!d_scratch || (reinterpret_cast<uintptr_t>(d_scratch) & 255) ||
+      scratch_bytes < sparse_scratch_bytes(g, slab_depth, &n_blocks))
+    return VOXTET_ERR_WORKSPACE;
+  // the dense slab inside the scratch stands in for the output buffer in the shared checks
+  uint32_t *dense = reinterpret_cast<uint32_t *>(static_cast<char *>(d_scratch) + align256(sizeof(SparseHeader)));
+  unsigned long long *block_counts = reinterpret_cast<unsigned long long *>(
+      reinterpret_cast<char *>(dense) + align256((size_t)slab_depth * g.ry * ((g.rx + 31) / 32) * 4));
+  SparseHeader *sh = static_cast<SparseHeader *>(d_scratch);
+  st = buffer_checks(n_verts, d_tets, n_tets, dense, d_workspace, ws_bytes);
+  if (st != VOXTET_OK) return st;
+  st = float_input_checks(d_verts, n_verts, grid_origin, voxel_size);
+  if (st != VOXTET_OK) return st;
+  cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
+  Workspace w;
+  workspace_bytes(n_tets, n_verts, &w, d_workspace);
+  if (cudaMemsetAsync(sh, 0, sizeof(SparseHeader), stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+  voxtet_opts inner = o;
+  inner.sync = 0;
+  inner.profile = 0;
+  const int W = (g.rx + 31) / 32;
+  for (int z0 = 0; z0 < g.rz; z0 += slab_depth) {
+    GridDims gs = g;
+    gs.z0 = z0;
+    gs.z1 = z0 + slab_depth < g.rz ? z0 + slab_depth : g.rz;
+    st = launch_prologue(w, dense, gs.out_words(), 1, stream);
+    if (st != VOXTET_OK) return st;
+    if (z0 == 0) {
+      st = launch_snap(w, d_verts, n_verts, grid_origin, voxel_size, g.K, stream);
+      if (st != VOXTET_OK) return st;
+    }
+    st = run_voxelize(w, n_verts, d_tets, n_tets, gs, dense, inner, stream);
+    if (st != VOXTET_OK) return st;
+    SlabBricks s;
+    s.dense = dense;
+    s.W = W;
+    s.ry = g.ry;
+    s.nz = gs.z1 - gs.z0;
+    s.nby = (g.ry + kBrickRows - 1) / kBrickRows;
+    s.nbz = (s.nz + kBrickSlices - 1) / kBrickSlices;
+    s.bz0 = z0 / kBrickSlices;
+    s.n = (long long)s.W * s.nby * s.nbz;
+    const long long nb = (s.n + kCompactBlock - 1) / kCompactBlock;
+    k_brick_count<<<(unsigned)nb, kCompactBlock, 0, stream>>>(s, block_counts);
+    k_brick_scan<<<1, 1024, 0, stream>>>(block_counts, nb, sh, w.hdr);
+    k_brick_write<<<(unsigned)nb, kCompactBlock, 0, stream>>>(s, block_counts, d_brick_keys, d_brick_words,
+                                                               (long long)max_bricks);
+    g_launches.fetch_add(3);
+    if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
+  }
+  if (cudaStreamSynchronize(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+  SparseHeader h;
+  if (cudaMemcpy(&h, sh, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return VOXTET_ERR_CUDA;
+  *n_bricks = (int64_t)h.total;
+  st = map_status_bits(h.sticky_bits);
+  if (st != VOXTET_OK) return st;
+  return h.total > (unsigned long long)max_bricks ? VOXTET_ERR_NOMEM : VOXTET_OK;
+}
+
+}  // extern "C"

@@ -26,7 +26,10 @@ EXPORTED = (
     "voxtet_last_status", "voxtet_read_stats", "voxtet_strerror", "voxtet_launch_count",
     "voxelize_tets_noalloc", "voxtet_batch_workspace_size", "voxelize_tets_batched", "voxtet_plan_create",
     "voxtet_plan_run", "voxtet_plan_query", "voxtet_plan_wait", "voxtet_plan_destroy",
+    "voxtet_sparse_scratch_size", "voxelize_tets_sparse",
 )
+SPARSE_MAX_SIDE = 65536
+BRICK_WORDS = 64
 NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
@@ -82,6 +85,12 @@ def load(path: Optional[str] = None):
         lib.voxelize_tets_grid.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, ctypes.POINTER(i32 * 3),
                                            i32, i32, P, P, sz, ctypes.POINTER(Opts), P]
         lib.voxelize_tets_grid.restype = ctypes.c_int
+        lib.voxtet_sparse_scratch_size.argtypes = [ctypes.POINTER(i32 * 3), i32]
+        lib.voxtet_sparse_scratch_size.restype = sz
+        lib.voxelize_tets_sparse.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, ctypes.POINTER(i32 * 3),
+                                             i32, P, P, i64, ctypes.POINTER(i64), P, sz, P, sz,
+                                             ctypes.POINTER(Opts), P]
+        lib.voxelize_tets_sparse.restype = ctypes.c_int
         lib.voxelize_tets_fixed.restype = ctypes.c_int
         lib.voxtet_last_status.argtypes = [P, P]
         lib.voxtet_last_status.restype = ctypes.c_int
@@ -267,6 +276,59 @@ def voxelize_grid(verts, tets, origin: Sequence[float], voxel_size: float, res3:
             raise VoxtetError(st)
         return out
     return st, out
+
+
+def sparse_scratch_size(res3: Sequence[int], slab_depth: int) -> int:
+    r3 = (ctypes.c_int32 * 3)(*[int(x) for x in res3])
+    return int(load().voxtet_sparse_scratch_size(ctypes.byref(r3), int(slab_depth)))
+
+
+def default_slab_depth(res3: Sequence[int], budget_bytes: int = 2 << 30) -> int:
+    """Slices per pass so that one dense slab stays within ``budget_bytes`` (a multiple of 8)."""
+    rx, ry, rz = (int(x) for x in res3)
+    per_slice = ry * ((rx + 31) // 32) * 4
+    d = max(8, min(rz, budget_bytes // max(per_slice, 1)) // 8 * 8)
+    return min(d, (rz + 7) // 8 * 8)
+
+
+def voxelize_sparse(verts, tets, origin: Sequence[float], voxel_size: float, res3: Sequence[int],
+                    slab_depth: int = 0, max_bricks: Optional[int] = None, workspace=None, scratch=None,
+                    mode: int = 0, use_filter: bool = True, span_rows: int = 0, row_cull: int = 0, stream=None):
+    """Brick-sparse grid: (keys int64 [n], words int32 [n, 64]) of the non-empty 32 x 8 x 8 bricks,
+    keys bx | by << 16 | bz << 32 in increasing order.  Grows the output and retries once if
+    ``max_bricks`` is too small."""
+    torch = _torch()
+    lib = load()
+    _check_cuda_tensor(verts, "verts", torch.float32)
+    _check_cuda_tensor(tets, "tets", torch.int32)
+    dev = verts.device
+    n_v, n_t = verts.shape[0], tets.shape[0]
+    r3 = (ctypes.c_int32 * 3)(*[int(x) for x in res3])
+    depth = int(slab_depth) or default_slab_depth(res3)
+    if scratch is None:
+        scratch = torch.empty(max(sparse_scratch_size(res3, depth), 256), dtype=torch.uint8, device=dev)
+    if workspace is None:
+        workspace = alloc_workspace(n_t, n_v, 1, dev)
+    if max_bricks is None:
+        rx, ry, rz = (int(x) for x in res3)
+        max_bricks = min(((rx + 31) // 32) * ((ry + 7) // 8) * ((rz + 7) // 8), 1 << 20)
+    o = make_opts(mode, False, use_filter, True, span_rows, row_cull=row_cull)
+    org = (ctypes.c_float * 3)(*[float(x) for x in origin])
+    for attempt in range(2):
+        keys = torch.empty(max(int(max_bricks), 1), dtype=torch.int64, device=dev)
+        words = torch.empty((max(int(max_bricks), 1), BRICK_WORDS), dtype=torch.int32, device=dev)
+        n = ctypes.c_int64(0)
+        st = lib.voxelize_tets_sparse(verts.data_ptr(), n_v, tets.data_ptr(), n_t, ctypes.byref(org),
+                                      float(voxel_size), ctypes.byref(r3), depth, keys.data_ptr(), words.data_ptr(),
+                                      int(max_bricks), ctypes.byref(n), scratch.data_ptr(), scratch.numel(),
+                                      workspace.data_ptr(), workspace.numel(), ctypes.byref(o), _stream_ptr(stream))
+        if st == ERR_NOMEM and attempt == 0:
+            max_bricks = int(n.value)
+            continue
+        if st != OK:
+            raise VoxtetError(st)
+        return keys[: n.value], words[: n.value]
+    raise VoxtetError(ERR_NOMEM)
 
 
 def last_status(workspace, stream=None) -> int:

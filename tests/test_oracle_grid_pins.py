@@ -149,3 +149,24 @@ def test_grid_error_codes(oracle_lib):
         with pytest.raises(oracle.OracleError) as e:
             oracle.voxelize_grid_fixed(xyz, t, (4, 4, 4), z0=z0, z1=z1)
         assert e.value.status == oracle.ERR_ARG
+
+
+@pytest.mark.parametrize("res3", [(50, 37, 61), (64, 64, 64), (33, 1, 7), (200, 9, 16)])
+def test_brick_conversion_round_trip(oracle_lib, res3):
+    """dense_to_bricks keeps every set bit, in the brick the layout names, and nothing else."""
+    v, t = mg.kuhn_lattice(4, 0.3, 11)
+    h = 1.0 / max(res3)
+    ext = np.array(res3, dtype=np.float64) * h
+    v = ((v.astype(np.float64) * 0.7 + 0.1) * ext).astype(np.float32)  # inside the grid, not filling it
+    g = oracle.voxelize_grid(v, t, (0, 0, 0), h, res3)
+    keys, words = oracle.dense_to_bricks(g, res3[0])
+    assert (np.diff(keys.astype(np.int64)) > 0).all()
+    assert words.any(axis=1).all()
+    assert (oracle.bricks_to_dense(keys, words, res3) == g).all()
+    occ = oracle.unpack_grid(g, res3[0])
+    assert int(np.unpackbits(words.view(np.uint8)).sum()) == int(occ.sum()) > 0
+    # one brick by hand: voxel (i, j, l) is bit i % 32 of word (l % 8) * 8 + j % 8 of brick (i//32, j//8, l//8)
+    l, j, i = [int(x[0]) for x in np.nonzero(occ)]
+    key = (i // 32) | ((j // 8) << 16) | ((l // 8) << 32)
+    row = words[np.searchsorted(keys, np.uint64(key))]
+    assert (int(row[(l % 8) * 8 + j % 8]) >> (i % 32)) & 1
