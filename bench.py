@@ -41,6 +41,7 @@ def parse_args():
     ap.add_argument("--slab", type=int, default=128, help="z-slices in the CPU oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-mesh batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) run")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the brick-sparse output run")
     ap.add_argument("--requests", type=int, default=10000, help="requests in the served run")
     ap.add_argument("--partition", choices=["replica", "slab"], default="replica",
                     help="N > 1: a replica of the whole job per rank (weak scaling), or one z-slab of the same "
@@ -341,6 +342,59 @@ def batched_section(args, flush, stream):
     }
 
 
+def sparse_section(stream):
+    """Brick-sparse output of torus_73 (198,549 tets) at 4096^3 and 8192^3: time, bricks and
+    bytes against the dense grid's; at 4096^3 the bricks are scattered back on the device and
+    compared bit for bit with the dense path's grid."""
+    import torch
+
+    from paper_2106_01326_gb300 import meshgen as mg
+    from paper_2106_01326_gb300 import voxtet as vt
+
+    cfg = mg.single_mesh_config("torus_73")
+    verts = torch.from_numpy(cfg["verts"]).cuda()
+    tets = torch.from_numpy(cfg["tets"]).cuda()
+    n_t, n_v = len(cfg["tets"]), len(cfg["verts"])
+    out = {"workload": f"torus_73: {n_t} tets (torus R=0.3, r=0.12 clipped from a 73^3 jittered Kuhn lattice)"}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for res in (4096, 8192):
+        res3 = (res, res, res)
+        ws = vt.alloc_workspace(n_t, n_v, res)
+        depth = vt.default_slab_depth(res3)
+        scratch = torch.empty(vt.sparse_scratch_size(res3, depth), dtype=torch.uint8, device="cuda")
+        keys, words = vt.voxelize_sparse(verts, tets, (0, 0, 0), 1.0 / res, res3, slab_depth=depth, workspace=ws,
+                                         scratch=scratch, stream=stream)
+        cap = int(len(keys))
+        times = []
+        for _ in range(3):
+            e0.record(stream)
+            keys, words = vt.voxelize_sparse(verts, tets, (0, 0, 0), 1.0 / res, res3, slab_depth=depth,
+                                             max_bricks=cap, workspace=ws, scratch=scratch, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        ms = statistics.median(times)
+        n_b = int(len(keys))
+        total_b = (res // 32) * (res // 8) * (res // 8)
+        entry = {"ms": ms, "tets_per_s": n_t / (ms / 1000.0), "gvox_per_s": res ** 3 / (ms / 1000.0) / 1e9,
+                 "slab_depth": depth, "slabs": -(-res // depth), "bricks": n_b, "bricks_fraction": n_b / total_b,
+                 "sparse_bytes": n_b * (8 + 4 * vt.BRICK_WORDS), "dense_bytes": res ** 3 // 8}
+        if res == 4096:
+            dense = vt.voxelize(verts, tets, (0, 0, 0), 1.0 / res, res, workspace=ws, stream=stream)
+            W = res // 32
+            b = dense.view(res // 8, 8, res // 8, 8, W).permute(0, 2, 4, 1, 3).reshape(-1, vt.BRICK_WORDS)
+            k = keys.view(torch.int64)
+            lin = ((k >> 32) * (res // 8) + ((k >> 16) & 0xFFFF)) * W + (k & 0xFFFF)
+            nonempty = b.ne(0).any(dim=1)
+            entry["bit_identical_to_dense"] = bool(int(nonempty.sum()) == n_b and torch.equal(b[lin], words))
+            del dense, b
+        entry["uncertain_rows_last_slab"] = int(vt.read_stats(ws)["fallback_rows"])
+        out[f"{res}^3"] = entry
+        del scratch, keys, words, ws
+        torch.cuda.empty_cache()
+    return out
+
+
 def served_section(args):
     """Continuous batching of a Poisson request stream over a pool of 16 device-resident
     meshes (1k-2M tets, log-uniform) at 64^3-512^3: capacity (all requests queued at
@@ -552,6 +606,8 @@ def run_ours(args):
         line["batched"] = batched_section(args, flush, stream)
     if not args.no_served:
         line["served"] = served_section(args)
+    if not args.no_sparse:
+        line["sparse"] = sparse_section(stream)
     if not args.no_cpu_baseline:
         import oracle
 

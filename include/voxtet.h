@@ -95,11 +95,16 @@ typedef struct {
 /* Fill *opts with the defaults listed above. */
 void voxtet_default_opts(voxtet_opts *opts);
 
-/* Bytes of device workspace a call with these sizes needs (the workspace must
- * be 256-byte aligned).  It holds a 256-byte status/counter header, the snapped
- * vertices (16 B per vertex), a queue of tetrahedra for the exact solver (4 B per
- * tetrahedron), a queue of rows the filter could not certify (8 B per entry,
- * max(65536, n_tets) entries) and a redo bitmap (1 bit per tetrahedron).
+/* Bytes of device workspace recommended for a call with these sizes (the workspace
+ * must be 256-byte aligned).  It holds a 256-byte status/counter header, the
+ * snapped vertices (16 B per vertex), a queue of tetrahedra for the exact solver
+ * (4 B per tetrahedron), a redo bitmap (1 bit per tetrahedron) and, last, a queue
+ * of rows the filter could not certify (8 B per entry): max(65536, n_tets)
+ * entries, or n_tets * (res / 512)^2 / 8 when res > 512 and that is more (fine
+ * grids leave more rows uncertain).  Calls accept any workspace of at least the
+ * res <= 512 size and give the row queue everything beyond it; when the queue
+ * overflows, the affected tetrahedra are re-solved whole with exact integers
+ * (correct, slower).  For general or sparse grids pass the longest side as res.
  * Returns 0 for negative sizes. */
 size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res);
 

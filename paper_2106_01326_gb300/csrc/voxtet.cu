@@ -56,6 +56,10 @@ constexpr int kBlock = 256;             // threads per block
 static __host__ __device__ int default_span_rows(int res) { return res >= 1024 ? 128 : 256; }
 constexpr int kCullMinRes = 256;        // automatic row culling from this resolution up
 constexpr int kMaxFilterRows = 8192;    // box rows per slice the fused kernel's slice table can hold
+// From this grid side up the filter clamps each face's bracket to the range where the
+// face can change a row (measured on GB300: 4% slower per row up to 1024^3 grids, where
+// few rows are uncertain; from 2048^3 it queues about 10x fewer rows and is faster)
+constexpr int kClampMinRes = 2048;
 
 // Workspace header (first 256 bytes of the workspace).
 struct Header {
@@ -440,7 +444,7 @@ constexpr int kMaxSlicesPerSpan = 16;
 // written to this thread's column of `tab` (b_lo | count << 16), then one flat loop
 // walks all candidate rows, so the lanes of a warp stay in step across slices.
 // Returns the rows visited.
-template <bool STRICT, bool CULL>
+template <bool STRICT, bool CULL, bool CLAMP>
 __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 V[4], const Box &bx, int c0, int c1,
                                              uint32_t (*tab)[kBlock], RowStage &stage) {
   if (v6_sign(V, kNarrowExtent) < 0) {  // orient (the tet is narrow: 64-bit sign)
@@ -557,8 +561,17 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
 #pragma unroll
     for (int m = 0; m < 4; ++m) {
       const float tt = __fmaf_rn(be[m], bf, ac[m]);
-      const float tl = __fsub_rd(tt, de[m]);
-      const float th = __fadd_ru(tt, de[m]);
+      const bool upm = m == 0 || (m == 1 && up1) || (m == 2 && up2);
+      float tl = __fsub_rd(tt, de[m]);
+      float th = __fadd_ru(tt, de[m]);
+      if (CLAMP) {
+        // only the part of the bracket where this face's bound can change the row counts:
+        // beyond it the bound is cut by the box or the row is empty whatever t is, so an
+        // integer there is no reason to queue the row (wide boxes of fine grids have large
+        // brackets on steep faces)
+        tl = fmaxf(tl, STRICT ? (upm ? 0.f : -fhi0) : (upm ? -1.f : -fhi0 - 1.f));
+        th = fminf(th, STRICT ? (upm ? fhi0 + 1.f : 1.f) : (upm ? fhi0 : 0.f));
+      }
       float v;
       if (STRICT) {
         const float cc = ceilf(tl);
@@ -569,7 +582,7 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
         amb |= f > tl;
         v = f;
       }
-      if (m == 0 || (m == 1 && up1) || (m == 2 && up2)) hi = fminf(hi, v);
+      if (upm) hi = fminf(hi, v);
       else lo = fmaxf(lo, -v);
     }
     const bool live = !amb && lo <= hi;
@@ -613,7 +626,7 @@ struct TileCounters {
 
 // Phases (1)-(4) for tets [base, base + kTile) of one mesh.  All threads of the block
 // call it; it begins and ends with the block in step.
-template <bool STRICT, bool CULL>
+template <bool STRICT, bool CULL, bool CLAMP>
 __device__ __forceinline__ void process_tile(const Params &p, long long base, long long end, TileSmem &sm,
                                              TileCounters &ctr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -733,7 +746,7 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
     tet_box(V, p.sh, p.rx, p.ry, p.z0, p.z1, bx);
     const int S = slices_per_span(p, bx.nb, bx.nc);
     const int c0 = (int)(sp - sm.off[a]) * S;
-    ctr.rows += run_span<STRICT, CULL>(p, t, V, bx, c0, min(c0 + S, bx.nc), sm.slice_tab, sm.stage);
+    ctr.rows += run_span<STRICT, CULL, CLAMP>(p, t, V, bx, c0, min(c0 + S, bx.nc), sm.slice_tab, sm.stage);
   }
   flush_stage(p, sm.stage);
 }
@@ -759,7 +772,7 @@ __device__ __forceinline__ void flush_counters(Header *hdr, TileCounters &ctr) {
   ctr = TileCounters();
 }
 
-template <bool STRICT, bool CULL>
+template <bool STRICT, bool CULL, bool CLAMP>
 __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p) {
   __shared__ TileSmem sm;
   __shared__ unsigned long long tile_s;
@@ -775,7 +788,7 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
     const long long base = tile < big ? tile * kTile : big * kTile + (tile - big) * kSmallTile;
     if (base >= p.n_tets) break;
     const long long end = min(p.n_tets, base + (tile < big ? kTile : kSmallTile));
-    process_tile<STRICT, CULL>(p, base, end, sm, ctr);
+    process_tile<STRICT, CULL, CLAMP>(p, base, end, sm, ctr);
   }
   flush_counters(p.hdr, ctr);
 }
@@ -996,8 +1009,8 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
     }
     const long long base = (long long)(tile_s - tile_base[j]) * kTile;
     const long long end = min(sp.n_tets, base + kTile);
-    if (sp.cull) process_tile<STRICT, true>(sp, base, end, sm, ctr);
-    else process_tile<STRICT, false>(sp, base, end, sm, ctr);
+    if (sp.cull) process_tile<STRICT, true, false>(sp, base, end, sm, ctr);
+    else process_tile<STRICT, false, false>(sp, base, end, sm, ctr);
   }
   if (cur >= 0) flush_counters(sp.hdr, ctr);
 }
@@ -1022,19 +1035,24 @@ static std::atomic<unsigned long long> g_launches{0};
 constexpr int kMaxDevices = 64;
 constexpr int kExactBlock = 128;
 typedef void (*VoxKernel)(Params);
-// k_voxelize variants indexed by (strict << 1) | cull
+// k_voxelize variants indexed by (strict << 2) | (cull << 1) | clamp
+constexpr int kVariants = 8;
 static VoxKernel voxelize_kernel(int idx) {
   switch (idx) {
-    case 0: return k_voxelize<false, false>;
-    case 1: return k_voxelize<false, true>;
-    case 2: return k_voxelize<true, false>;
-    default: return k_voxelize<true, true>;
+    case 0: return k_voxelize<false, false, false>;
+    case 1: return k_voxelize<false, false, true>;
+    case 2: return k_voxelize<false, true, false>;
+    case 3: return k_voxelize<false, true, true>;
+    case 4: return k_voxelize<true, false, false>;
+    case 5: return k_voxelize<true, false, true>;
+    case 6: return k_voxelize<true, true, false>;
+    default: return k_voxelize<true, true, true>;
   }
 }
 
 struct DeviceInfo {
   int sms = 0;
-  int occ[4] = {0, 0, 0, 0};  // resident blocks per SM of each k_voxelize variant
+  int occ[kVariants] = {};  // resident blocks per SM of each k_voxelize variant
   bool ready = false;
 };
 static DeviceInfo g_dev[kMaxDevices];
@@ -1078,7 +1096,7 @@ static cudaError_t device_info(DeviceInfo *&out) {
     }
     if (!d.ready) {
       e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
-      for (int v = 0; v < 4 && e == cudaSuccess; ++v)
+      for (int v = 0; v < kVariants && e == cudaSuccess; ++v)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[v], voxelize_kernel(v), kBlock, 0);
       if (e == cudaSuccess) d.ready = true;
     }
@@ -1135,18 +1153,26 @@ struct Workspace {
   long long redo_words;
 };
 
-static size_t workspace_bytes(long long n_tets, long long n_verts, Workspace *w, void *base) {
-  const unsigned long long q = row_queue_capacity(n_tets);
+// Layout: header, snapped vertices, tet queue, redo bitmap, row queue.  The row queue
+// comes last and takes whatever the caller's workspace holds beyond the minimum
+// (ws_bytes; 0 = the minimum), so a larger workspace means fewer whole-tet redos.
+static size_t workspace_bytes(long long n_tets, long long n_verts, Workspace *w, void *base, size_t ws_bytes = 0) {
+  unsigned long long q = row_queue_capacity(n_tets);
   const long long redo_words = (n_tets + 31) / 32;
   size_t o = sizeof(Header);
   const size_t o_v = o;
   o += align256((size_t)n_verts * sizeof(int4));
   const size_t o_t = o;
   o += align256((size_t)n_tets * sizeof(uint32_t));
-  const size_t o_r = o;
-  o += align256((size_t)q * sizeof(RowItem));
   const size_t o_b = o;
   o += align256((size_t)redo_words * sizeof(uint32_t));
+  const size_t o_r = o;
+  o += align256((size_t)q * sizeof(RowItem));
+  if (ws_bytes > o) {
+    unsigned long long more = (ws_bytes - o_r) / sizeof(RowItem);
+    if (more > 0xFFFFFFFFull) more = 0xFFFFFFFFull;
+    if (more > q) q = more;
+  }
   if (w) {
     char *c = reinterpret_cast<char *>(base);
     w->hdr = reinterpret_cast<Header *>(c);
@@ -1210,7 +1236,8 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     p.span_rows = o.span_rows > 0 ? o.span_rows : default_span_rows(g.longest());
     p.exact_all = o.use_filter ? 0 : 1;
     const bool cull = o.row_cull == 1 || (o.row_cull == 0 && g.longest() >= kCullMinRes);
-    const int variant = (o.mode == 1 ? 2 : 0) | (cull ? 1 : 0);
+    const bool clamp = g.longest() >= kClampMinRes;
+    const int variant = (o.mode == 1 ? 4 : 0) | (cull ? 2 : 0) | (clamp ? 1 : 0);
     long long grid = (long long)dev->sms * (dev->occ[variant] > 0 ? dev->occ[variant] : 1);
     const long long tail = 2 * grid * kSmallTile;
     p.big_tiles = n_tets > tail ? (n_tets - tail) / kTile : 0;
@@ -1329,9 +1356,18 @@ void voxtet_default_opts(voxtet_opts *o) {
 }
 
 size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res) {
-  (void)res;
   if (n_tets < 0 || n_verts < 0) return 0;
-  return workspace_bytes(n_tets, n_verts, nullptr, nullptr);
+  const size_t minimum = workspace_bytes(n_tets, n_verts, nullptr, nullptr);
+  // Uncertain rows grow with the rows a tet spans, about (res / 512)^2 for a given mesh:
+  // from 1024 up the row queue gets n_tets * (res / 512)^2 / 8 entries (measured on the
+  // sliver and torus workloads: 0.4-0.9 uncertain rows per tet at 1024^3-8192^3 with the
+  // clamped filter), so that a queue overflow and whole-tet redos stay rare.
+  if (res <= 512) return minimum;
+  const double scale = (double)res / 512.0;
+  const double want = (double)n_tets * scale * scale / 8.0;
+  const unsigned long long q = want > 4.0e9 ? 4000000000ull : (unsigned long long)want;
+  if (q <= row_queue_capacity(n_tets)) return minimum;
+  return minimum + align256((size_t)(q - row_queue_capacity(n_tets)) * sizeof(RowItem));
 }
 
 int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
@@ -1346,7 +1382,7 @@ int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, 
   if (st != VOXTET_OK) return st;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   Workspace w;
-  workspace_bytes(n_tets, n_verts, &w, d_workspace);
+  workspace_bytes(n_tets, n_verts, &w, d_workspace, ws_bytes);
   const GridDims g = cubic_dims(res, k);
   st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
   if (st != VOXTET_OK) return st;
@@ -1374,7 +1410,7 @@ int voxelize_tets_grid(const float *d_verts, int64_t n_verts, const int32_t *d_t
   if (st != VOXTET_OK) return st;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   Workspace w;
-  workspace_bytes(n_tets, n_verts, &w, d_workspace);
+  workspace_bytes(n_tets, n_verts, &w, d_workspace, ws_bytes);
   st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
   if (st != VOXTET_OK) return st;
   st = launch_snap(w, d_verts, n_verts, grid_origin, voxel_size, g.K, stream);
@@ -1393,7 +1429,7 @@ int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_
   if (n_verts > 0 && (!d_xyz || (reinterpret_cast<uintptr_t>(d_xyz) & 3))) return VOXTET_ERR_ARG;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   Workspace w;
-  workspace_bytes(n_tets, n_verts, &w, d_workspace);
+  workspace_bytes(n_tets, n_verts, &w, d_workspace, ws_bytes);
   const GridDims g = cubic_dims(res, k);
   st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
   if (st != VOXTET_OK) return st;
@@ -1533,7 +1569,7 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
     const voxtet_job &J = jobs[j];
     const long long nt = ok[j] ? J.n_tets : 0, nv = ok[j] ? J.n_verts : 0;
     Workspace w;
-    workspace_bytes(nt, nv, &w, ws_dev + off);
+    workspace_bytes(nt, nv, &w, ws_dev + off, ok[j] ? job_slice_bytes(J, true) : 0);
     off += job_slice_bytes(J, ok[j]);
     JobDesc &d = tab[j];
     std::memset(&d, 0, sizeof(d));
@@ -1818,7 +1854,8 @@ extern "C" int voxelize_tets_noalloc(const float *d_verts, int64_t n_verts, cons
                                      const float grid_origin[3], float voxel_size, int32_t res,
                                      uint32_t *d_out_bits, const voxtet_opts *opts, void *stream) {
   if (n_tets < 0 || n_verts < 0) return VOXTET_ERR_ARG;
-  if (voxtet_workspace_size(n_tets, n_verts, res) > (size_t)VOXTET_NOALLOC_SCRATCH_BYTES) return VOXTET_ERR_NOMEM;
+  // the minimum workspace must fit; the row queue then takes the rest of the scratch
+  if (voxtet_workspace_size(n_tets, n_verts, 1) > (size_t)VOXTET_NOALLOC_SCRATCH_BYTES) return VOXTET_ERR_NOMEM;
   voxtet_opts o;
   resolve_opts(opts, o);
   o.profile = 0;  // profiling would create CUDA events
@@ -1845,7 +1882,7 @@ namespace voxtet {
 constexpr int kBrickRows = 8;                        // y rows per brick
 constexpr int kBrickSlices = 8;                      // z slices per brick
 constexpr int kBrickWords = kBrickRows * kBrickSlices;
-constexpr int kCompactBlock = 256;
+constexpr int kCompactBlock = 128;
 
 struct SparseHeader {
   unsigned long long total;  // non-empty bricks of all slabs so far (may exceed the capacity)
@@ -1934,12 +1971,28 @@ __global__ void __launch_bounds__(1024) k_brick_scan(unsigned long long *counts,
   if (tid == 0) sh->total = carry;
 }
 
+// Each warp stages its 32 consecutive bricks' row-words in shared memory (lane l loads
+// word r of brick l: a warp-wide load of row r is one contiguous run), then writes
+// every non-empty brick with two 128-byte stores.
 __global__ void __launch_bounds__(kCompactBlock) k_brick_write(SlabBricks s, const unsigned long long *block_offsets,
                                                                uint64_t *keys, uint32_t *words, long long cap) {
+  __shared__ uint32_t stage[kCompactBlock / 32][kBrickWords][33];
   __shared__ unsigned warp_base[kCompactBlock / 32];
   const long long b = (long long)blockIdx.x * kCompactBlock + threadIdx.x;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const bool ne = b < s.n && brick_nonempty(s, b);
+  uint32_t acc = 0;
+  int bx = 0, by = 0, bz = 0;
+  if (b < s.n) {
+    int ny, nz;
+    const uint32_t *o = brick_origin(s, b, bx, by, bz, ny, nz);
+    for (int dz = 0; dz < kBrickSlices; ++dz)
+      for (int dy = 0; dy < kBrickRows; ++dy) {
+        const uint32_t v = (dz < nz && dy < ny) ? o[((size_t)dz * s.ry + dy) * s.W] : 0u;
+        stage[warp][dz * kBrickRows + dy][lane] = v;
+        acc |= v;
+      }
+  }
+  const bool ne = acc != 0;
   const unsigned m = __ballot_sync(0xFFFFFFFFu, ne);
   if (lane == 0) warp_base[warp] = __popc(m);
   __syncthreads();
@@ -1952,17 +2005,21 @@ __global__ void __launch_bounds__(kCompactBlock) k_brick_write(SlabBricks s, con
     }
   }
   __syncthreads();
-  if (!ne) return;
-  const unsigned long long slot =
-      block_offsets[blockIdx.x] + warp_base[warp] + (unsigned long long)__popc(m & ((1u << lane) - 1u));
-  if (slot >= (unsigned long long)cap) return;
-  int bx, by, bz, ny, nz;
-  const uint32_t *o = brick_origin(s, b, bx, by, bz, ny, nz);
-  keys[slot] = (uint64_t)bx | ((uint64_t)by << 16) | ((uint64_t)(s.bz0 + bz) << 32);
-  uint32_t *dst = words + slot * kBrickWords;
-  for (int dz = 0; dz < kBrickSlices; ++dz)
-    for (int dy = 0; dy < kBrickRows; ++dy)
-      dst[dz * kBrickRows + dy] = (dz < nz && dy < ny) ? o[((size_t)dz * s.ry + dy) * s.W] : 0u;
+  const unsigned long long first = block_offsets[blockIdx.x] + warp_base[warp];
+  if (ne) {
+    const unsigned long long slot = first + (unsigned long long)__popc(m & ((1u << lane) - 1u));
+    if (slot < (unsigned long long)cap)
+      keys[slot] = (uint64_t)bx | ((uint64_t)by << 16) | ((uint64_t)(s.bz0 + bz) << 32);
+  }
+  unsigned mm = m;
+  for (unsigned long long slot = first; mm; ++slot) {
+    const int j = __ffs(mm) - 1;
+    mm &= mm - 1;
+    if (slot >= (unsigned long long)cap) break;
+    uint32_t *dst = words + slot * kBrickWords;
+    dst[lane] = stage[warp][lane][j];
+    dst[32 + lane] = stage[warp][32 + lane][j];
+  }
 }
 
 // Scratch: header, one dense slab, the per-block counts of a slab's bricks.
@@ -2033,7 +2090,7 @@ int voxelize_tets_sparse(const float *d_verts, int64_t n_verts, const int32_t *d
   if (st != VOXTET_OK) return st;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   Workspace w;
-  workspace_bytes(n_tets, n_verts, &w, d_workspace);
+  workspace_bytes(n_tets, n_verts, &w, d_workspace, ws_bytes);
   if (cudaMemsetAsync(sh, 0, sizeof(SparseHeader), stream) != cudaSuccess) return VOXTET_ERR_CUDA;
   voxtet_opts inner = o;
   inner.sync = 0;

@@ -264,7 +264,7 @@ def voxelize_grid(verts, tets, origin: Sequence[float], voxel_size: float, res3:
         out = alloc_grid_dims(res3, (z0, z1), verts.device)  # an empty slab passes a NULL pointer
     _check_cuda_tensor(out, "out", torch.int32)
     if workspace is None:
-        workspace = alloc_workspace(n_t, n_v, 1, verts.device)
+        workspace = alloc_workspace(n_t, n_v, max(int(x) for x in res3), verts.device)
     o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull)
     org = (ctypes.c_float * 3)(*[float(x) for x in origin])
     r3 = (ctypes.c_int32 * 3)(rx, ry, rz)
@@ -308,7 +308,7 @@ def voxelize_sparse(verts, tets, origin: Sequence[float], voxel_size: float, res
     if scratch is None:
         scratch = torch.empty(max(sparse_scratch_size(res3, depth), 256), dtype=torch.uint8, device=dev)
     if workspace is None:
-        workspace = alloc_workspace(n_t, n_v, 1, dev)
+        workspace = alloc_workspace(n_t, n_v, max(int(x) for x in res3), dev)
     if max_bricks is None:
         rx, ry, rz = (int(x) for x in res3)
         max_bricks = min(((rx + 31) // 32) * ((ry + 7) // 8) * ((rz + 7) // 8), 1 << 20)
