@@ -101,6 +101,7 @@ struct Params {
   int exact_all;    // 1: every tet goes to the exact kernel
   int cull;         // 1: skip rows outside each slice's cross-section (batched kernel)
   long long big_tiles;  // single-mesh launch: tiles of kTile tets before the kSmallTile tail
+  long long tile_stride;  // > 0: tile k holds tets k + j * tile_stride (slab launches), else contiguous tiles
 };
 
 // Row-queue capacity for a mesh of n_tets tets.
@@ -626,7 +627,16 @@ struct TileCounters {
 
 // Phases (1)-(4) for tets [base, base + kTile) of one mesh.  All threads of the block
 // call it; it begins and ends with the block in step.
-template <bool STRICT, bool CULL, bool CLAMP>
+// Tet in slot i of the tile that starts at `base`: base + i, or, in a slab launch
+// (STRIDED, base = the tile's number), base + i * tile_stride, so that the tets of the
+// slab -- one contiguous run in a mesh numbered along z -- spread over every tile.
+template <bool STRIDED>
+__device__ __forceinline__ long long tile_tet(const Params &p, long long base, long long i) {
+  return STRIDED ? base + i * p.tile_stride : base + i;
+}
+
+// Slots whose tet is at or past `end` are empty.
+template <bool STRICT, bool CULL, bool CLAMP, bool STRIDED>
 __device__ __forceinline__ void process_tile(const Params &p, long long base, long long end, TileSmem &sm,
                                              TileCounters &ctr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -637,7 +647,7 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
   float wlo = 3.0e38f, whi = 0.f;
 #pragma unroll
   for (int k = 0; k < kPerThread; ++k) {
-    const long long t = base + (long long)tid * kPerThread + k;
+    const long long t = tile_tet<STRIDED>(p, base, (long long)tid * kPerThread + k);
     work[k] = 0.f;
     cnt[k] = t < end ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide, work[k]) : 0u;
     if (cnt[k]) {
@@ -738,7 +748,7 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
       if (sm.off[mid] <= sp) a = mid;
       else bnd = mid - 1;
     }
-    const long long t = base + a;
+    const long long t = tile_tet<STRIDED>(p, base, a);
     int3 V[4];
     Box bx;
     int dummy = 0;
@@ -772,7 +782,7 @@ __device__ __forceinline__ void flush_counters(Header *hdr, TileCounters &ctr) {
   ctr = TileCounters();
 }
 
-template <bool STRICT, bool CULL, bool CLAMP>
+template <bool STRICT, bool CULL, bool CLAMP, bool STRIDED>
 __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p) {
   __shared__ TileSmem sm;
   __shared__ unsigned long long tile_s;
@@ -785,10 +795,15 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
     if (threadIdx.x == 0) tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
     __syncthreads();
     const long long tile = (long long)tile_s;
+    if (STRIDED) {
+      if (tile >= p.tile_stride) break;
+      process_tile<STRICT, CULL, CLAMP, true>(p, tile, p.n_tets, sm, ctr);
+      continue;
+    }
     const long long base = tile < big ? tile * kTile : big * kTile + (tile - big) * kSmallTile;
     if (base >= p.n_tets) break;
     const long long end = min(p.n_tets, base + (tile < big ? kTile : kSmallTile));
-    process_tile<STRICT, CULL, CLAMP>(p, base, end, sm, ctr);
+    process_tile<STRICT, CULL, CLAMP, false>(p, base, end, sm, ctr);
   }
   flush_counters(p.hdr, ctr);
 }
@@ -1009,8 +1024,8 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
     }
     const long long base = (long long)(tile_s - tile_base[j]) * kTile;
     const long long end = min(sp.n_tets, base + kTile);
-    if (sp.cull) process_tile<STRICT, true, false>(sp, base, end, sm, ctr);
-    else process_tile<STRICT, false, false>(sp, base, end, sm, ctr);
+    if (sp.cull) process_tile<STRICT, true, false, false>(sp, base, end, sm, ctr);
+    else process_tile<STRICT, false, false, false>(sp, base, end, sm, ctr);
   }
   if (cur >= 0) flush_counters(sp.hdr, ctr);
 }
@@ -1035,19 +1050,23 @@ static std::atomic<unsigned long long> g_launches{0};
 constexpr int kMaxDevices = 64;
 constexpr int kExactBlock = 128;
 typedef void (*VoxKernel)(Params);
-// k_voxelize variants indexed by (strict << 2) | (cull << 1) | clamp
-constexpr int kVariants = 8;
-static VoxKernel voxelize_kernel(int idx) {
+// k_voxelize variants indexed by (strided << 3) | (strict << 2) | (cull << 1) | clamp
+constexpr int kVariants = 16;
+template <bool STRIDED>
+static VoxKernel voxelize_kernel_s(int idx) {
   switch (idx) {
-    case 0: return k_voxelize<false, false, false>;
-    case 1: return k_voxelize<false, false, true>;
-    case 2: return k_voxelize<false, true, false>;
-    case 3: return k_voxelize<false, true, true>;
-    case 4: return k_voxelize<true, false, false>;
-    case 5: return k_voxelize<true, false, true>;
-    case 6: return k_voxelize<true, true, false>;
-    default: return k_voxelize<true, true, true>;
+    case 0: return k_voxelize<false, false, false, STRIDED>;
+    case 1: return k_voxelize<false, false, true, STRIDED>;
+    case 2: return k_voxelize<false, true, false, STRIDED>;
+    case 3: return k_voxelize<false, true, true, STRIDED>;
+    case 4: return k_voxelize<true, false, false, STRIDED>;
+    case 5: return k_voxelize<true, false, true, STRIDED>;
+    case 6: return k_voxelize<true, true, false, STRIDED>;
+    default: return k_voxelize<true, true, true, STRIDED>;
   }
+}
+static VoxKernel voxelize_kernel(int idx) {
+  return idx & 8 ? voxelize_kernel_s<true>(idx & 7) : voxelize_kernel_s<false>(idx & 7);
 }
 
 struct DeviceInfo {
@@ -1237,11 +1256,20 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     p.exact_all = o.use_filter ? 0 : 1;
     const bool cull = o.row_cull == 1 || (o.row_cull == 0 && g.longest() >= kCullMinRes);
     const bool clamp = g.longest() >= kClampMinRes;
-    const int variant = (o.mode == 1 ? 4 : 0) | (cull ? 2 : 0) | (clamp ? 1 : 0);
+    const bool strided = g.z1 - g.z0 < g.rz;
+    const int variant = (strided ? 8 : 0) | (o.mode == 1 ? 4 : 0) | (cull ? 2 : 0) | (clamp ? 1 : 0);
     long long grid = (long long)dev->sms * (dev->occ[variant] > 0 ? dev->occ[variant] : 1);
     const long long tail = 2 * grid * kSmallTile;
     p.big_tiles = n_tets > tail ? (n_tets - tail) / kTile : 0;
-    const long long tiles = p.big_tiles + (n_tets - p.big_tiles * kTile + kSmallTile - 1) / kSmallTile;
+    long long tiles = p.big_tiles + (n_tets - p.big_tiles * kTile + kSmallTile - 1) / kSmallTile;
+    // a slab of the grid: strided tiles, so the slab's tets (often one contiguous run of a
+    // mesh numbered by z) are shared by every block (measured on GB300: an 8192^3 grid in
+    // slabs of 256 slices ran at half the speed of the whole grid with contiguous tiles)
+    p.tile_stride = 0;
+    if (strided) {
+      p.tile_stride = (n_tets + kTile - 1) / kTile;
+      tiles = p.tile_stride;
+    }
     if (grid > tiles) grid = tiles;
     if (o.profile && profile_begin(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
     voxelize_kernel(variant)<<<(unsigned)grid, kBlock, 0, stream>>>(p);
@@ -1917,8 +1945,13 @@ __device__ __forceinline__ bool brick_nonempty(const SlabBricks &s, long long b)
   int bx, by, bz, ny, nz;
   const uint32_t *o = brick_origin(s, b, bx, by, bz, ny, nz);
   uint32_t acc = 0;
-  for (int dz = 0; dz < nz; ++dz)
-    for (int dy = 0; dy < ny; ++dy) acc |= o[((size_t)dz * s.ry + dy) * s.W];
+  if (ny == kBrickRows && nz == kBrickSlices) {  // whole brick: 64 independent loads in flight
+#pragma unroll
+    for (int r = 0; r < kBrickWords; ++r) acc |= o[((size_t)(r >> 3) * s.ry + (r & 7)) * s.W];
+  } else {
+    for (int dz = 0; dz < nz; ++dz)
+      for (int dy = 0; dy < ny; ++dy) acc |= o[((size_t)dz * s.ry + dy) * s.W];
+  }
   return acc != 0;
 }
 
@@ -1985,12 +2018,21 @@ __global__ void __launch_bounds__(kCompactBlock) k_brick_write(SlabBricks s, con
   if (b < s.n) {
     int ny, nz;
     const uint32_t *o = brick_origin(s, b, bx, by, bz, ny, nz);
-    for (int dz = 0; dz < kBrickSlices; ++dz)
-      for (int dy = 0; dy < kBrickRows; ++dy) {
-        const uint32_t v = (dz < nz && dy < ny) ? o[((size_t)dz * s.ry + dy) * s.W] : 0u;
-        stage[warp][dz * kBrickRows + dy][lane] = v;
+    if (ny == kBrickRows && nz == kBrickSlices) {
+#pragma unroll
+      for (int r = 0; r < kBrickWords; ++r) {
+        const uint32_t v = o[((size_t)(r >> 3) * s.ry + (r & 7)) * s.W];
+        stage[warp][r][lane] = v;
         acc |= v;
       }
+    } else {
+      for (int dz = 0; dz < kBrickSlices; ++dz)
+        for (int dy = 0; dy < kBrickRows; ++dy) {
+          const uint32_t v = (dz < nz && dy < ny) ? o[((size_t)dz * s.ry + dy) * s.W] : 0u;
+          stage[warp][dz * kBrickRows + dy][lane] = v;
+          acc |= v;
+        }
+    }
   }
   const bool ne = acc != 0;
   const unsigned m = __ballot_sync(0xFFFFFFFFu, ne);
