@@ -196,6 +196,14 @@ int voxelize_tets_sparse(const float *d_verts, int64_t n_verts, const int32_t *d
  * this workspace recorded (VOXTET_OK if none). */
 int voxtet_last_status(const void *d_workspace, void *stream);
 
+/* Without synchronizing: enqueue on `stream` a copy of the device-detected status
+ * word the last call on this workspace left (4 bytes) into *status_word, which may
+ * be pinned host or device memory; once the stream has passed that point,
+ * voxtet_status_of_word(*status_word) is that call's device-detected status.  For
+ * callers that keep many calls in flight (a pipeline of host meshes). */
+int voxtet_status_async(const void *d_workspace, int32_t *status_word, void *stream);
+int voxtet_status_of_word(int32_t status_word);
+
 /* Synchronize `stream` and copy the last call's counters to *out (HOST). */
 int voxtet_read_stats(const void *d_workspace, voxtet_stats *out, void *stream);
 

@@ -1481,6 +1481,15 @@ int voxtet_last_status(const void *d_workspace, void *stream_) {
   return map_status_bits(bits);
 }
 
+int voxtet_status_async(const void *d_workspace, int32_t *status_word, void *stream_) {
+  if (!d_workspace || !status_word) return VOXTET_ERR_ARG;
+  const cudaError_t e = cudaMemcpyAsync(status_word, &reinterpret_cast<const Header *>(d_workspace)->status_bits,
+                                        sizeof(int32_t), cudaMemcpyDefault, reinterpret_cast<cudaStream_t>(stream_));
+  return e == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
+}
+
+int voxtet_status_of_word(int32_t status_word) { return map_status_bits(status_word); }
+
 int voxtet_read_stats(const void *d_workspace, voxtet_stats *out, void *stream_) {
   if (!d_workspace || !out) return VOXTET_ERR_ARG;
   if (cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream_)) != cudaSuccess) return VOXTET_ERR_CUDA;

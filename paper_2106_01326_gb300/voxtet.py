@@ -26,7 +26,7 @@ EXPORTED = (
     "voxtet_last_status", "voxtet_read_stats", "voxtet_strerror", "voxtet_launch_count",
     "voxelize_tets_noalloc", "voxtet_batch_workspace_size", "voxelize_tets_batched", "voxtet_plan_create",
     "voxtet_plan_run", "voxtet_plan_query", "voxtet_plan_wait", "voxtet_plan_destroy",
-    "voxtet_sparse_scratch_size", "voxelize_tets_sparse",
+    "voxtet_sparse_scratch_size", "voxelize_tets_sparse", "voxtet_status_async", "voxtet_status_of_word",
 )
 SPARSE_MAX_SIDE = 65536
 BRICK_WORDS = 64
@@ -85,6 +85,10 @@ def load(path: Optional[str] = None):
         lib.voxelize_tets_grid.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, ctypes.POINTER(i32 * 3),
                                            i32, i32, P, P, sz, ctypes.POINTER(Opts), P]
         lib.voxelize_tets_grid.restype = ctypes.c_int
+        lib.voxtet_status_async.argtypes = [P, P, P]
+        lib.voxtet_status_async.restype = ctypes.c_int
+        lib.voxtet_status_of_word.argtypes = [i32]
+        lib.voxtet_status_of_word.restype = ctypes.c_int
         lib.voxtet_sparse_scratch_size.argtypes = [ctypes.POINTER(i32 * 3), i32]
         lib.voxtet_sparse_scratch_size.restype = sz
         lib.voxelize_tets_sparse.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, ctypes.POINTER(i32 * 3),
