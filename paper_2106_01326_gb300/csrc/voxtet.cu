@@ -544,6 +544,10 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
   float bf = 0.f, ac[4];
   uint32_t *row = p.out;
   const float fhi0 = (float)(bx.na - 1);
+  // row (b, k) of the span is row00 + k * slice_words + b * W; the offset stays below
+  // 16 slices of a grid slice (< 2^32 words for every accepted grid)
+  uint32_t *const row00 = p.out + ((size_t)(bx.l0 - p.z0 + c0) * p.ry + bx.j0) * p.W;
+  const unsigned slice_words = (unsigned)p.ry * (unsigned)p.W;
   for (unsigned r = 0; r < total; ++r) {
     if (b == b_end) {
       const uint32_t e = tab[m_tab][tid];
@@ -555,7 +559,7 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
       const float cf = (float)(c0 + k);
 #pragma unroll
       for (int m = 0; m < 4; ++m) ac[m] = __fmaf_rn(ga[m], cf, al[m]);
-      row = p.out + ((size_t)(bx.l0 - p.z0 + c0 + k) * p.ry + (bx.j0 + b)) * p.W;
+      row = row00 + ((unsigned)k * slice_words + (unsigned)b * (unsigned)p.W);
     }
     float lo = 0.f, hi = fhi0;
     bool amb = false;
