@@ -236,7 +236,8 @@ def add_slivers(
 
 # ---------------------------------------------------------------- single-mesh workloads
 
-def coplanar_face_soup(n_tets: int, res: int, seed: int, spread: int) -> Tuple[np.ndarray, np.ndarray]:
+def coplanar_face_soup(n_tets: int, res: int, seed: int, spread: int,
+                       region: Optional[Sequence[Tuple[int, int]]] = None) -> Tuple[np.ndarray, np.ndarray]:
     """Tie-heavy tet soup on the lattice of a cubic 2^k grid (int32 lattice coordinates, tets).
 
     Each tet has one face on a plane n . X = n . P through a voxel-centre sample P
@@ -245,7 +246,8 @@ def coplanar_face_soup(n_tets: int, res: int, seed: int, spread: int) -> Tuple[n
     zero.  The face's three vertices and the fourth vertex lie within ``spread``
     voxels of P at unaligned lattice points, so the zeros only appear after
     cancellation of large products -- the case where inexact arithmetic picks signs
-    at random.  All coordinates stay within 2^21.
+    at random.  All coordinates stay within 2^21.  ``region`` ((x0, x1), (y0, y1), (z0, z1)),
+    in sample indices, limits where the planes' samples P are drawn (default: the whole grid).
     """
     k = res.bit_length() - 1
     if res < 1 or (1 << k) != res:
@@ -256,7 +258,8 @@ def coplanar_face_soup(n_tets: int, res: int, seed: int, spread: int) -> Tuple[n
     tets: List[List[int]] = []
     lim = 1 << 21
     while len(tets) < n_tets:
-        P = (2 * rng.integers(0, res, size=3) + 1) * s
+        lo_hi = region if region is not None else ((0, res), (0, res), (0, res))
+        P = (2 * np.array([rng.integers(a, b) for a, b in lo_hi], dtype=np.int64) + 1) * s
         nrm = rng.integers(-3, 4, size=3)
         if not nrm.any():
             continue

@@ -126,6 +126,18 @@ def test_coplanar_face_ties(vt, res, spread, n):
             assert (got == ref).all(), (mode, use_filter)
 
 
+@pytest.mark.parametrize("mode", [0, 1])
+def test_coplanar_face_ties_clamped_filter(vt, mode):
+    """2048^3: the filter clamps each face's bracket to where the face can change a row; ties
+    placed on planes through samples must still come out exact at the clamp boundaries."""
+    res = 2048
+    xyz, tets = mg.coplanar_face_soup(300, res, seed=77 + mode, spread=24)
+    ref = oracle.voxelize_fixed(xyz, tets, res, mode=mode)
+    got = gpu_fixed(vt, xyz, tets, res, mode=mode)
+    assert (got == ref).all()
+    assert ref.any()
+
+
 def test_wide_tets_128bit_path(vt):
     """Tets wider than 2^20 lattice units take the 128-bit exact path."""
     rng = np.random.default_rng(7)

@@ -118,3 +118,17 @@ def test_sparse_capacity_and_errors(vt):
     # no tets: no bricks
     e_keys, e_words = vt.voxelize_sparse(dv, dt[:0], (0, 0, 0), h, res3)
     assert len(e_keys) == 0 and e_words.shape == (0, vt.BRICK_WORDS)
+
+
+def test_sparse_coplanar_ties_wide_grid(vt):
+    """Tie-heavy soup (faces on planes through samples) in a 4096 x 256 x 64 grid through the
+    sparse path (clamped filter, strided slab tiles), against the oracle's bricks."""
+    import torch
+
+    res3 = (4096, 256, 64)
+    xyz, tets = mg.coplanar_face_soup(400, 4096, seed=31, spread=20, region=((0, 4096), (24, 232), (24, 40)))
+    h = 1.0 / 4096
+    v = (xyz.astype(np.float64) * (h / 256)).astype(np.float32)  # lattice step 2^(20-12) = 256 per voxel
+    assert (v.astype(np.float64) * (256 / h) == xyz).all()  # exact round trip: the snap gives xyz back
+    _check(vt, v, tets, h, res3, slab_depth=16)
+    _check(vt, v, tets, h, res3, slab_depth=24, mode=1)
