@@ -99,6 +99,7 @@ struct Params {
   int sh;           // log2 of the lattice step per voxel, 20 - ceil(log2(longest side))
   int span_rows;    // target bounding-box rows per span
   int exact_all;    // 1: every tet goes to the exact kernel
+  int max_slices;   // slices a span may hold (16 or 32): the slice table's rows in dynamic shared memory
   int cull;         // 1: skip rows outside each slice's cross-section (batched kernel)
   long long big_tiles;  // single-mesh launch: tiles of kTile tets before the kSmallTile tail
   long long tile_stride;  // > 0: tile k holds tets k + j * tile_stride (slab launches), else contiguous tiles
@@ -246,7 +247,7 @@ __device__ __forceinline__ int oriented_tet(const Params &p, long long t, int3 V
 // thread's slice table).  Equal spans keep the per-span work estimate meaningful.
 __device__ __forceinline__ int slices_per_span(const Params &p, int nb, int nc) {
   int S = p.span_rows / nb;
-  S = S < 1 ? 1 : (S > 16 ? 16 : S);
+  S = S < 1 ? 1 : (S > p.max_slices ? p.max_slices : S);
   const int n = (nc + S - 1) / S;
   return (nc + n - 1) / n;
 }
@@ -438,7 +439,14 @@ __device__ __forceinline__ int small_float_to_int(float f) {
   return __float_as_int(__fadd_rn(f, 8388608.0f)) - 0x4B000000;
 }
 
-constexpr int kMaxSlicesPerSpan = 16;
+// Slices per span: the slice table (one column per thread, in dynamic shared memory)
+// has p.max_slices rows.  16 rows fit 512^3 grids, where a tet spans about 9 slices; from
+// 1024^3 a tet spans 17 or more and 32 rows let one span hold it, so the spans sorted by
+// the per-tet work estimate are even (measured on GB300: 1024^3 kernel 1.49 -> 1.18 ms;
+// at 512^3 the larger table costs 1.5 %, the L1 it takes).
+constexpr int kMaxSlicesPerSpan = 32;
+constexpr size_t kSliceTableBytesMax = (size_t)kMaxSlicesPerSpan * kBlock * sizeof(uint32_t);
+static size_t slice_table_bytes(int max_slices) { return (size_t)max_slices * kBlock * sizeof(uint32_t); }
 
 // Phases (3)+(4): slices [c0, c1) (at most kMaxSlicesPerSpan) of a narrow tet whose
 // four faces all depend on x.  First the candidate rows of every slice are found and
@@ -515,8 +523,8 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
   }
   const int tid = threadIdx.x;
   const int ns = c1 - c0;
-  // slice table: only slices with candidate rows, packed k | b_lo << 4 | n << 18
-  // (k < 16 slices, b_lo and n < 2^14)
+  // slice table: only slices with candidate rows, packed k | b_lo << 5 | (n - 1) << 19
+  // (k < 32 slices, b_lo < 2^14, n <= 8192 rows)
   unsigned total = 0;
   int nt = 0;
   {
@@ -530,7 +538,7 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
       if (nz > 1) narrow_by_row_constraint<STRICT>(zL1 + zDz1 * (i64)(c0 + k), zDy1, b_lo, b_hi);
       if (b_hi >= b_lo) {
         const int n = b_hi - b_lo + 1;
-        tab[nt][tid] = (uint32_t)k | ((uint32_t)b_lo << 4) | ((uint32_t)n << 18);
+        tab[nt][tid] = (uint32_t)k | ((uint32_t)b_lo << 5) | ((uint32_t)(n - 1) << 19);
         ++nt;
         total += (unsigned)n;
       }
@@ -552,9 +560,9 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
     if (b == b_end) {
       const uint32_t e = tab[m_tab][tid];
       ++m_tab;
-      const int k = (int)(e & 15u);
-      b = (int)((e >> 4) & 0x3FFFu);
-      b_end = b + (int)(e >> 18);
+      const int k = (int)(e & 31u);
+      b = (int)((e >> 5) & 0x3FFFu);
+      b_end = b + 1 + (int)(e >> 19);
       bf = (float)b;
       const float cf = (float)(c0 + k);
 #pragma unroll
@@ -596,7 +604,7 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
     const int x0 = bx.i0 + small_float_to_int(lo);
     const int x1 = bx.i0 + small_float_to_int(hi);
     or_span_lanes(row, x0, x1, live);
-    if (amb) queue_row_staged(p, stage, t, b, c0 + (int)(tab[m_tab - 1][tid] & 15u));
+    if (amb) queue_row_staged(p, stage, t, b, c0 + (int)(tab[m_tab - 1][tid] & 31u));
     ++b;
     bf += 1.f;
     row += p.W;
@@ -616,7 +624,6 @@ constexpr int kBuckets = 32;
 struct TileSmem {
   uint32_t off[kTile + 1];
   uint32_t warp_tot[kBlock / 32];
-  uint32_t slice_tab[kMaxSlicesPerSpan][kBlock];
   uint16_t order[kSortedSpans];  // spans by estimated work
   uint32_t bucket[kBuckets];
   float wmin, wmax;
@@ -642,7 +649,7 @@ __device__ __forceinline__ long long tile_tet(const Params &p, long long base, l
 // Slots whose tet is at or past `end` are empty.
 template <bool STRICT, bool CULL, bool CLAMP, bool STRIDED>
 __device__ __forceinline__ void process_tile(const Params &p, long long base, long long end, TileSmem &sm,
-                                             TileCounters &ctr) {
+                                             uint32_t (*slice_tab)[kBlock], TileCounters &ctr) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   // (1) classification and span counts of this thread's kPerThread consecutive tets
   uint32_t cnt[kPerThread];
@@ -760,7 +767,7 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
     tet_box(V, p.sh, p.rx, p.ry, p.z0, p.z1, bx);
     const int S = slices_per_span(p, bx.nb, bx.nc);
     const int c0 = (int)(sp - sm.off[a]) * S;
-    ctr.rows += run_span<STRICT, CULL, CLAMP>(p, t, V, bx, c0, min(c0 + S, bx.nc), sm.slice_tab, sm.stage);
+    ctr.rows += run_span<STRICT, CULL, CLAMP>(p, t, V, bx, c0, min(c0 + S, bx.nc), slice_tab, sm.stage);
   }
   flush_stage(p, sm.stage);
 }
@@ -786,9 +793,16 @@ __device__ __forceinline__ void flush_counters(Header *hdr, TileCounters &ctr) {
   ctr = TileCounters();
 }
 
+// The slice table lives in dynamic shared memory: p.max_slices rows of kBlock words.
+__device__ __forceinline__ uint32_t (*dynamic_slice_table())[kBlock] {
+  extern __shared__ uint32_t voxtet_dyn_smem[];
+  return reinterpret_cast<uint32_t (*)[kBlock]>(voxtet_dyn_smem);
+}
+
 template <bool STRICT, bool CULL, bool CLAMP, bool STRIDED>
 __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p) {
   __shared__ TileSmem sm;
+  uint32_t (*const slice_tab)[kBlock] = dynamic_slice_table();
   __shared__ unsigned long long tile_s;
   TileCounters ctr;
   if (threadIdx.x == 0) sm.stage.n = 0;
@@ -801,13 +815,13 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
     const long long tile = (long long)tile_s;
     if (STRIDED) {
       if (tile >= p.tile_stride) break;
-      process_tile<STRICT, CULL, CLAMP, true>(p, tile, p.n_tets, sm, ctr);
+      process_tile<STRICT, CULL, CLAMP, true>(p, tile, p.n_tets, sm, slice_tab, ctr);
       continue;
     }
     const long long base = tile < big ? tile * kTile : big * kTile + (tile - big) * kSmallTile;
     if (base >= p.n_tets) break;
     const long long end = min(p.n_tets, base + (tile < big ? kTile : kSmallTile));
-    process_tile<STRICT, CULL, CLAMP, false>(p, base, end, sm, ctr);
+    process_tile<STRICT, CULL, CLAMP, false>(p, base, end, sm, slice_tab, ctr);
   }
   flush_counters(p.hdr, ctr);
 }
@@ -1002,6 +1016,7 @@ template <bool STRICT>
 __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
     k_voxelize_batched(BatchHeader *bh, const JobDesc *jobs, const unsigned long long *tile_base) {
   __shared__ TileSmem sm;
+  uint32_t (*const slice_tab)[kBlock] = dynamic_slice_table();
   __shared__ Params sp;
   __shared__ unsigned long long tile_s;
   __shared__ int job_s;
@@ -1028,8 +1043,8 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
     }
     const long long base = (long long)(tile_s - tile_base[j]) * kTile;
     const long long end = min(sp.n_tets, base + kTile);
-    if (sp.cull) process_tile<STRICT, true, false, false>(sp, base, end, sm, ctr);
-    else process_tile<STRICT, false, false, false>(sp, base, end, sm, ctr);
+    if (sp.cull) process_tile<STRICT, true, false, false>(sp, base, end, sm, slice_tab, ctr);
+    else process_tile<STRICT, false, false, false>(sp, base, end, sm, slice_tab, ctr);
   }
   if (cur >= 0) flush_counters(sp.hdr, ctr);
 }
@@ -1119,8 +1134,13 @@ static cudaError_t device_info(DeviceInfo *&out) {
     }
     if (!d.ready) {
       e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
-      for (int v = 0; v < kVariants && e == cudaSuccess; ++v)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[v], voxelize_kernel(v), kBlock, 0);
+      for (int v = 0; v < kVariants && e == cudaSuccess; ++v) {
+        e = cudaFuncSetAttribute(reinterpret_cast<const void *>(voxelize_kernel(v)),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSliceTableBytesMax);
+        if (e == cudaSuccess)
+          e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[v], voxelize_kernel(v), kBlock,
+                                                            kSliceTableBytesMax);
+      }
       if (e == cudaSuccess) d.ready = true;
     }
     g_dev_lock.store(0);
@@ -1257,6 +1277,7 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     p.W = (g.rx + 31) / 32;
     p.sh = kLatticeBits - g.K;
     p.span_rows = o.span_rows > 0 ? o.span_rows : default_span_rows(g.longest());
+    p.max_slices = g.longest() >= 1024 ? 32 : 16;
     p.exact_all = o.use_filter ? 0 : 1;
     const bool cull = o.row_cull == 1 || (o.row_cull == 0 && g.longest() >= kCullMinRes);
     const bool clamp = g.longest() >= kClampMinRes;
@@ -1276,7 +1297,7 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     }
     if (grid > tiles) grid = tiles;
     if (o.profile && profile_begin(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
-    voxelize_kernel(variant)<<<(unsigned)grid, kBlock, 0, stream>>>(p);
+    voxelize_kernel(variant)<<<(unsigned)grid, kBlock, slice_table_bytes(p.max_slices), stream>>>(p);
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
     if (o.profile) {
@@ -1626,6 +1647,7 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
     d.p.rowq = w.rowq;
     d.p.redo = w.redo;
     d.p.q_cap = w.q_cap;
+    d.p.max_slices = 16;  // batch jobs are small grids (see kMaxSlicesPerSpan)
     d.p.rx = res;
     d.p.ry = res;
     d.p.z0 = 0;
@@ -1679,12 +1701,14 @@ static int launch_batch(char *ws, int cap, int strict, cudaStream_t stream) {
   k_snap_batched<<<g8, 256, 0, stream>>>(bh, tab, vbase);
   int occ = 0;
   if (strict) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<true>, kBlock, 0);
-    k_voxelize_batched<true><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, 0, stream>>>(bh, tab, tiles);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<true>, kBlock, slice_table_bytes(16));
+    k_voxelize_batched<true><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, slice_table_bytes(16), stream>>>(
+        bh, tab, tiles);
     k_exact_batched<true><<<(unsigned)dev->sms * 4, kExactBlock, 0, stream>>>(bh, tab);
   } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<false>, kBlock, 0);
-    k_voxelize_batched<false><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, 0, stream>>>(bh, tab, tiles);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<false>, kBlock, slice_table_bytes(16));
+    k_voxelize_batched<false><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, slice_table_bytes(16), stream>>>(
+        bh, tab, tiles);
     k_exact_batched<false><<<(unsigned)dev->sms * 4, kExactBlock, 0, stream>>>(bh, tab);
   }
   k_gather_status<<<(cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, 256, 0, stream>>>(bh, tab, status);
