@@ -51,9 +51,9 @@ namespace voxtet {
 
 constexpr int kBlock = 256;             // threads per block
 // Bounding-box rows per span (whole z-slices) when the caller does not choose: measured
-// on GB300, 256 is best up to 512^3 grids and 128 from 1024^3 (smaller spans balance
-// the larger boxes of fine grids better).
-static __host__ __device__ int default_span_rows(int res) { return res >= 1024 ? 128 : 256; }
+// on GB300, 256 is best up to 512^3 grids; from 1024^3 (32-slice spans) 1024 keeps a
+// typical tet in one span, whose work estimate then sorts the lanes evenly.
+static __host__ __device__ int default_span_rows(int res) { return res >= 1024 ? 1024 : 256; }
 constexpr int kCullMinRes = 256;        // automatic row culling from this resolution up
 constexpr int kMaxFilterRows = 8192;    // box rows per slice the fused kernel's slice table can hold
 // From this grid side up the filter clamps each face's bracket to the range where the
