@@ -552,8 +552,8 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
   float bf = 0.f, ac[4];
   uint32_t *row = p.out;
   const float fhi0 = (float)(bx.na - 1);
-  // row (b, k) of the span is row00 + k * slice_words + b * W; the offset stays below
-  // 16 slices of a grid slice (< 2^32 words for every accepted grid)
+  // row (b, k) of the span is row00 + k * slice_words + b * W; with k < 32 and b < ry the
+  // offset is below 32 * ry * W <= 32 * 65536 * 2048 = 2^32 words for every accepted grid
   uint32_t *const row00 = p.out + ((size_t)(bx.l0 - p.z0 + c0) * p.ry + bx.j0) * p.W;
   const unsigned slice_words = (unsigned)p.ry * (unsigned)p.W;
   for (unsigned r = 0; r < total; ++r) {
