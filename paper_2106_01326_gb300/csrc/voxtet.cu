@@ -50,10 +50,12 @@ namespace voxtet {
 #endif
 
 constexpr int kBlock = 256;             // threads per block
-// Bounding-box rows per span (whole z-slices) when the caller does not choose: measured
-// on GB300, 256 is best up to 512^3 grids; from 1024^3 (32-slice spans) 1024 keeps a
-// typical tet in one span, whose work estimate then sorts the lanes evenly.
-static __host__ __device__ int default_span_rows(int res) { return res >= 1024 ? 1024 : 256; }
+// Bounding-box rows per span (whole z-slices) when the caller does not choose (the
+// autotuner picks per mesh).  Measured on GB300 with the sliver and torus meshes: 256 is
+// best or within 13 % of it at every size except 1024^3, where 1024 (with 32-slice
+// spans) keeps a typical tet in one span, whose work estimate then sorts the lanes
+// evenly (sliver mesh 1.49 -> 1.15 ms); from 2048^3 spans that long can take twice as long.
+static __host__ __device__ int default_span_rows(int res) { return res >= 1024 && res < 2048 ? 1024 : 256; }
 constexpr int kCullMinRes = 256;        // automatic row culling from this resolution up
 constexpr int kMaxFilterRows = 8192;    // box rows per slice the fused kernel's slice table can hold
 // From this grid side up the filter clamps each face's bracket to the range where the
