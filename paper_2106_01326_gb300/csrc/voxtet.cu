@@ -753,7 +753,12 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
 
   // (3)+(4) spans (by estimated work when sorted); the tet slot of span sp is the
   // largest u with off[u] <= sp
-  for (uint32_t i = tid; i < total; i += kBlock) {
+  // Rounds of kBlock spans, dealt forwards and backwards in turn: each warp still gets 32
+  // neighbouring spans of the work order, and no thread takes the largest of every round
+  // (the block waits at the tile's end for its slowest thread).
+  for (uint32_t r0 = 0; r0 < total; r0 += kBlock) {
+    const uint32_t i = r0 + (((r0 / kBlock) & 1u) ? (uint32_t)(kBlock - 1 - tid) : (uint32_t)tid);
+    if (i >= total) continue;
     const uint32_t sp = sorted ? (uint32_t)sm.order[i] : i;
     int a = 0, bnd = kTile - 1;
     while (a < bnd) {
