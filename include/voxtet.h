@@ -73,7 +73,8 @@ typedef struct {
     int32_t accumulate; /* 0 = clear out_bits first (default), 1 = OR into its current contents */
     int32_t use_filter; /* 1 = single-precision filter + exact fallback (default), 0 = exact integer only */
     int32_t sync;       /* 1 = synchronize the stream and return device-detected status (default 1) */
-    int32_t span_rows;  /* bounding-box x-rows per work item (whole z-slices); 0 = automatic */
+    int32_t span_rows;  /* bounding-box x-rows per work item (whole z-slices, at most 16 of them, 32 when the
+                           grid's longest side is 1024 or more); 0 = automatic */
     int32_t block;      /* threads per block of the scanline kernel; 0 = automatic (only 256 is accepted) */
     int32_t profile;    /* 1 = record CUDA events around the main kernel on `stream` (see voxtet_stats) */
     int32_t row_cull;   /* skip x-rows outside each z-slice's cross-section: 0 = automatic, 1 = on, 2 = off */
@@ -87,8 +88,8 @@ typedef struct {
     uint64_t degenerate_tets; /* tetrahedra with zero signed volume (skipped) */
     uint64_t wide_tets;       /* tetrahedra wider than 2^20 lattice units (128-bit exact path) */
     uint64_t kernel_ns;       /* device time of the main kernel of the last profiled call on this thread, else 0 */
-    uint64_t exact_tets;      /* tetrahedra solved entirely with exact integers (wide, a face parallel to x,
-                                 or use_filter = 0) */
+    uint64_t exact_tets;      /* tetrahedra solved entirely with exact integers (wider than 2^20 lattice
+                                 units, boxes taller than 8192 rows, or use_filter = 0) */
     uint64_t reserved;
 } voxtet_stats;
 
