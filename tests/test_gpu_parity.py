@@ -314,3 +314,24 @@ def test_max_resolution_sampled(vt):
     assert int(torch.count_nonzero(g[:zmin])) == 0 and int(torch.count_nonzero(g[zmax:])) == 0
     del g
     torch.cuda.empty_cache()
+
+
+def test_max_mesh_size_full_lattice(vt):
+    """48,000,000 tets (the unjittered 200^3 Kuhn lattice over the grid) at 512^3: a conforming
+    tiling of the grid's cube, so its closed union sets every one of the 134 M bits -- a closed
+    form at a size that exercises the 32-bit tet queues, tile counters and row queue."""
+    import torch
+
+    ijk, tets = mg.kuhn_lattice_int(200)
+    verts = torch.from_numpy((ijk.astype(np.float32) / np.float32(200))).cuda()
+    del ijk
+    dt = torch.from_numpy(tets).cuda()
+    del tets
+    res = 512
+    ws = vt.alloc_workspace(dt.shape[0], verts.shape[0], res)
+    g = vt.voxelize(verts, dt, (0, 0, 0), 1.0 / res, res, workspace=ws)
+    st = vt.read_stats(ws)
+    assert st["degenerate_tets"] == 0
+    assert bool((g == -1).all())  # every 32-bit word all ones
+    del g, ws, verts, dt
+    torch.cuda.empty_cache()
