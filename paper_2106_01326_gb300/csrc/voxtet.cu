@@ -2006,6 +2006,44 @@ __global__ void __launch_bounds__(kCompactBlock) k_brick_count(SlabBricks s, uns
   if (threadIdx.x == 0) block_counts[blockIdx.x] = (unsigned long long)c;
 }
 
+// The same counts when rows hold a multiple of 4 words: a thread takes 4 neighbouring
+// bricks (one 16-byte load per row), so a warp covers the 128 bricks of one write block
+// and a warp-wide load reads 512 contiguous bytes.
+__global__ void __launch_bounds__(kCompactBlock) k_brick_count4(SlabBricks s, unsigned long long *block_counts,
+                                                                long long n_blocks) {
+  const long long gt = (long long)blockIdx.x * kCompactBlock + threadIdx.x;
+  const long long b0 = gt * 4;
+  unsigned c = 0;
+  if (b0 < s.n) {
+    int bx, by, bz, ny, nz;
+    const uint32_t *o = brick_origin(s, b0, bx, by, bz, ny, nz);
+    uint32_t a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+    if (ny == kBrickRows && nz == kBrickSlices) {
+#pragma unroll
+      for (int r = 0; r < kBrickWords; ++r) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(o + ((size_t)(r >> 3) * s.ry + (r & 7)) * s.W);
+        a0 |= v.x;
+        a1 |= v.y;
+        a2 |= v.z;
+        a3 |= v.w;
+      }
+    } else {
+      for (int dz = 0; dz < nz; ++dz)
+        for (int dy = 0; dy < ny; ++dy) {
+          const uint4 v = *reinterpret_cast<const uint4 *>(o + ((size_t)dz * s.ry + dy) * s.W);
+          a0 |= v.x;
+          a1 |= v.y;
+          a2 |= v.z;
+          a3 |= v.w;
+        }
+    }
+    c = (a0 != 0) + (a1 != 0) + (a2 != 0) + (a3 != 0);
+  }
+  c = __reduce_add_sync(0xFFFFFFFFu, c);
+  const long long wb = gt >> 5;  // this warp's write block
+  if ((threadIdx.x & 31) == 0 && wb < n_blocks) block_counts[wb] = (unsigned long long)c;
+}
+
 // One block: exclusive scan of the block counts in place, offset by the running total,
 // which then advances; the slab's device-detected status bits join the sticky bits.
 __global__ void __launch_bounds__(1024) k_brick_scan(unsigned long long *counts, long long n_blocks,
@@ -2204,7 +2242,13 @@ int voxelize_tets_sparse(const float *d_verts, int64_t n_verts, const int32_t *d
     s.bz0 = z0 / kBrickSlices;
     s.n = (long long)s.W * s.nby * s.nbz;
     const long long nb = (s.n + kCompactBlock - 1) / kCompactBlock;
-    k_brick_count<<<(unsigned)nb, kCompactBlock, 0, stream>>>(s, block_counts);
+    if (s.W % 4 == 0) {
+      const long long threads = s.n / 4;
+      k_brick_count4<<<(unsigned)((threads + kCompactBlock - 1) / kCompactBlock), kCompactBlock, 0, stream>>>(
+          s, block_counts, nb);
+    } else {
+      k_brick_count<<<(unsigned)nb, kCompactBlock, 0, stream>>>(s, block_counts);
+    }
     k_brick_scan<<<1, 1024, 0, stream>>>(block_counts, nb, sh, w.hdr);
     k_brick_write<<<(unsigned)nb, kCompactBlock, 0, stream>>>(s, block_counts, d_brick_keys, d_brick_words,
                                                                (long long)max_bricks);
