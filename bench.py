@@ -42,6 +42,7 @@ def parse_args():
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-mesh batched comparison")
     ap.add_argument("--no-served", action="store_true", help="skip the served (continuous batching) run")
     ap.add_argument("--no-sparse", action="store_true", help="skip the brick-sparse output run")
+    ap.add_argument("--no-slabs", action="store_true", help="skip the one-GPU estimate of z-slab strong scaling")
     ap.add_argument("--requests", type=int, default=10000, help="requests in the served run")
     ap.add_argument("--partition", choices=["replica", "slab"], default="replica",
                     help="N > 1: a replica of the whole job per rank (weak scaling), or one z-slab of the same "
@@ -395,6 +396,56 @@ def sparse_section(stream):
     return out
 
 
+def slab_section(verts, tets, cfg, span_rows, row_cull, stream):
+    """The benchmark grid cut into 2, 4 and 8 weighted z-slabs (slabs.slab_cuts over the tets per
+    slice), each slab voxelized from the tets that can reach it (slabs.tets_for_slab) and timed
+    alone on this GPU: the slowest slab against the whole grid estimates the strong scaling of one
+    slab per GPU, since ranks exchange nothing."""
+    import torch
+
+    from paper_2106_01326_gb300 import slabs
+    from paper_2106_01326_gb300 import voxtet as vt
+
+    res = cfg["res"]
+    n_t, n_v = len(cfg["tets"]), len(cfg["verts"])
+    ws = vt.alloc_workspace(n_t, n_v, res)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, reps=5):
+        fn()
+        ts = []
+        for _ in range(reps):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return statistics.median(ts)
+
+    full = vt.alloc_grid(res)
+    full_ms = timed(lambda: vt.voxelize(verts, tets, cfg["origin"], cfg["voxel_size"], res, out=full, workspace=ws,
+                                        sync=False, span_rows=span_rows, row_cull=row_cull, stream=stream))
+    w = slabs.slice_weights(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"], res)
+    out = {"whole_grid_ms": full_ms}
+    for n in (2, 4, 8):
+        times, parts, n_sub = [], [], []
+        for z0, z1 in slabs.slab_cuts(res, n, w):
+            g = vt.alloc_grid_dims((res, res, res), (z0, z1))
+            # the rank's tets (chosen once per mesh on the host, not timed)
+            sub = torch.from_numpy(slabs.tets_for_slab(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"],
+                                                       z0, z1)).to(tets.device)
+            n_sub.append(int(sub.shape[0]))
+            times.append(timed(lambda g=g, z0=z0, z1=z1, sub=sub: vt.voxelize_grid(
+                verts, sub, cfg["origin"], cfg["voxel_size"], (res, res, res), z_range=(z0, z1), out=g,
+                workspace=ws, sync=False, span_rows=span_rows, row_cull=row_cull, stream=stream)))
+            parts.append(g)
+        same = bool(torch.equal(torch.cat(parts, dim=0), full))
+        out[f"{n}_slabs"] = {"slab_ms": [round(t, 4) for t in times], "max_slab_ms": max(times), "tets_per_slab": n_sub,
+                             "strong_scaling_estimate": full_ms / (n * max(times)), "concatenation_equals_grid": same}
+        del parts
+    return out
+
+
 def served_section(args):
     """Continuous batching of a Poisson request stream over a pool of 16 device-resident
     meshes (1k-2M tets, log-uniform) at 64^3-512^3: capacity (all requests queued at
@@ -476,6 +527,8 @@ def run_ours(args):
         w = slabs.slice_weights(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"], res)
         z_range = slabs.rank_slab(res, rank, world, w)
         grid = vt.alloc_grid_dims((res, res, res), z_range, dev)
+        tets = torch.from_numpy(slabs.tets_for_slab(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"],
+                                                    *z_range)).to(dev)
     else:
         z_range = (0, res)
         grid = vt.alloc_grid(res, dev)
@@ -540,7 +593,7 @@ def run_ours(args):
 
     # end to end through the public API: pinned host mesh -> device, voxelize, grid -> pinned host
     h_verts = torch.from_numpy(cfg["verts"]).pin_memory()
-    h_tets = torch.from_numpy(cfg["tets"]).pin_memory()
+    h_tets = tets.cpu().pin_memory()  # this rank's tets (a slab's subset under --partition slab)
     h_grid = torch.empty(grid.shape, dtype=torch.int32).pin_memory()
     d_verts = torch.empty_like(verts)
     d_tets = torch.empty_like(tets)
@@ -634,6 +687,8 @@ def run_ours(args):
         line["served"] = served_section(args)
     if not args.no_sparse:
         line["sparse"] = sparse_section(stream)
+    if not args.no_slabs and world == 1:
+        line["slabs_one_gpu"] = slab_section(verts, tets, cfg, span_rows, row_cull, stream)
     if not args.no_cpu_baseline:
         import oracle
 

@@ -60,6 +60,19 @@ def slice_weights(verts: np.ndarray, tets: np.ndarray, origin: Sequence[float], 
     return np.cumsum(d)[:rz]
 
 
+def tets_for_slab(verts: np.ndarray, tets: np.ndarray, origin: Sequence[float], voxel_size: float, z0: int,
+                  z1: int) -> np.ndarray:
+    """The tets that may have samples in slices [z0, z1): a superset (one slice of margin on each
+    side covers the difference between world coordinates and their snapped lattice points), so a
+    rank that voxelizes its slab from these alone gets the same bits as from the whole mesh."""
+    t = np.asarray(tets).reshape(-1, 4)
+    z = np.asarray(verts, dtype=np.float64)[:, 2][t]
+    lo = np.floor((z.min(axis=1) - float(origin[2])) / float(voxel_size)) - 1
+    hi = np.ceil((z.max(axis=1) - float(origin[2])) / float(voxel_size)) + 1
+    keep = (hi >= z0) & (lo <= z1 - 1)
+    return np.ascontiguousarray(t[keep])
+
+
 def rank_slab(rz: int, rank: int, world: int, weights: Optional[Sequence[float]] = None) -> Tuple[int, int]:
     """This rank's (z0, z1)."""
     return slab_cuts(rz, world, weights)[rank]

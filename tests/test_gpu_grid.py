@@ -122,3 +122,23 @@ def test_grid_errors(vt):
     # an empty slab is a valid call that writes nothing
     g = vt.voxelize_grid(dv, dt, (0, 0, 0), h, (8, 8, 8), z_range=(4, 4))
     assert g.shape == (0, 8, 1)
+
+
+def test_slabs_from_their_tet_subsets(vt):
+    """A rank voxelizes its slab from slabs.tets_for_slab alone: the slabs still concatenate to the
+    grid of the whole mesh (the subset is a superset of the tets that reach the slab)."""
+    import torch
+
+    from paper_2106_01326_gb300 import slabs
+
+    res3 = (128, 96, 120)
+    v, t, h = _mesh_for(res3, N=10, seed=13)
+    dv, dt = _dev(v, t)
+    full = vt.voxelize_grid(dv, dt, (0, 0, 0), h, res3)
+    w = slabs.slice_weights(v, t, (0, 0, 0), h, res3[2])
+    parts = []
+    for z0, z1 in slabs.slab_cuts(res3[2], 5, w):
+        sub = slabs.tets_for_slab(v, t, (0, 0, 0), h, z0, z1)
+        assert len(sub) < len(t)
+        parts.append(vt.voxelize_grid(dv, torch.from_numpy(sub).cuda(), (0, 0, 0), h, res3, z_range=(z0, z1)))
+    assert torch.equal(torch.cat(parts, dim=0), full)
