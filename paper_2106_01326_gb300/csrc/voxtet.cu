@@ -134,8 +134,12 @@ __global__ void k_prologue(Header *hdr, uint32_t *redo, long long redo_words, ui
 // X = round_half_even(((double)v - o) / h * 2^(20-k)), each double operation rounded to
 // nearest.  When h is a power of two the quotient is exact and the host passes
 // mul = 2^(20-k) / h instead (identical result, no double division).
+// With a zero origin and mul = 2^m, m >= 0 (fast = 1), ((double)v - 0) * mul is exact in
+// float as well (a power-of-two scale of a float, overflow aside, which the range check
+// catches), and rintf rounds half to even like the double path: the same X on the FP32
+// pipe instead of GB300's narrow FP64 unit.
 __global__ void k_snap(const float *__restrict__ v, long long n, double ox, double oy, double oz, double h,
-                       double scale, double mul, int use_mul, int4 *__restrict__ out, Header *hdr) {
+                       double scale, double mul, int use_mul, int fast, int4 *__restrict__ out, Header *hdr) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   int err = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -149,6 +153,16 @@ __global__ void k_snap(const float *__restrict__ v, long long n, double ox, doub
       if (!isfinite(f)) {
         flag = 1;
         err |= kErrNan;
+        continue;
+      }
+      if (fast) {
+        const float r = rintf(__fmul_rn(f, (float)mul));
+        if (!(fabsf(r) <= (float)kCoordLimit)) {
+          flag = 1;
+          err |= kErrRange;
+          continue;
+        }
+        X[q] = (int)r;
         continue;
       }
       const double d = __dsub_rn((double)f, o[q]);
@@ -913,6 +927,7 @@ struct SnapArgs {
   double ox, oy, oz, h, scale, mul;
   int use_mul;
   int fixed;  // 1: vertices are int32 lattice coordinates (range check only)
+  int fast;   // 1: zero origin and mul = 2^m, m >= 0: the snap in float (as in k_snap)
 };
 
 struct ZeroArgs {
@@ -1001,6 +1016,16 @@ __global__ void k_snap_batched(const BatchHeader *bh, const JobDesc *jobs, const
         if (!isfinite(f)) {
           flag = 1;
           err |= kErrNan;
+          continue;
+        }
+        if (d.s.fast) {
+          const float rf = rintf(__fmul_rn(f, (float)d.s.mul));
+          if (!(fabsf(rf) <= (float)kCoordLimit)) {
+            flag = 1;
+            err |= kErrRange;
+            continue;
+          }
+          X[q] = (int)rf;
           continue;
         }
         const double dd = __dsub_rn((double)f, o[q]);
@@ -1388,9 +1413,11 @@ static int launch_snap(const Workspace &w, const float *d_verts, long long n_ver
   const double mant = std::frexp(h, &e2);
   const int use_mul = mant == 0.5 ? 1 : 0;
   const double mul = use_mul ? std::ldexp(1.0, kLatticeBits - K - (e2 - 1)) : 0.0;
+  const int fast = use_mul && mul >= 1.0 && mul <= 0x1p100 && grid_origin[0] == 0.0f && grid_origin[1] == 0.0f &&
+                   grid_origin[2] == 0.0f;
   k_snap<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(
       d_verts, n_verts, (double)grid_origin[0], (double)grid_origin[1], (double)grid_origin[2], h, scale, mul,
-      use_mul, w.verts4, w.hdr);
+      use_mul, fast, w.verts4, w.hdr);
   g_launches.fetch_add(1);
   return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
 }
@@ -1685,6 +1712,8 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
       const double mant = std::frexp(d.s.h, &e2);
       d.s.use_mul = mant == 0.5 ? 1 : 0;
       d.s.mul = d.s.use_mul ? std::ldexp(1.0, kLatticeBits - k - (e2 - 1)) : 0.0;
+      d.s.fast = d.s.use_mul && d.s.mul >= 1.0 && d.s.mul <= 0x1p100 && J.origin[0] == 0.0f && J.origin[1] == 0.0f &&
+                 J.origin[2] == 0.0f;
     }
     d.z.grid_words = ok[j] ? (long long)res * res * d.p.W : 0;
     d.z.clear = (ok[j] && !o.accumulate) ? 1 : 0;
