@@ -335,3 +335,18 @@ def test_max_mesh_size_full_lattice(vt):
     assert bool((g == -1).all())  # every 32-bit word all ones
     del g, ws, verts, dt
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("res", [64, 512])
+def test_snap_ties_zero_origin(vt, res):
+    """Vertices exactly half a lattice unit off: with origin 0 and h = 1/res the snap runs in
+    float and must round half to even exactly as the oracle's double arithmetic does."""
+    v, t = mg.kuhn_lattice(4, 0.3, res)
+    half = np.rint(v.astype(np.float64) * 2.0 ** 20) + 0.5  # (k + 1/2) lattice units
+    v = (half * 2.0 ** -20).astype(np.float32)
+    assert (v.astype(np.float64) * 2.0 ** 20 % 1 == 0.5).all()  # every coordinate is a tie
+    st, xyz = oracle.snap(v, (0, 0, 0), 1.0 / res, res)
+    assert st == 0 and (xyz % 2 == 0).all()  # ties went to even
+    got = gpu_world(vt, v, t, (0, 0, 0), 1.0 / res, res)
+    ref = oracle.voxelize(v, t, (0, 0, 0), 1.0 / res, res)
+    assert (got == ref).all()
