@@ -2003,15 +2003,15 @@ struct SparseHeader {
 static_assert(sizeof(SparseHeader) == 256, "sparse header is 256 bytes");
 
 struct SlabBricks {
-  const uint32_t *dense;  // [nz][ry][W] words of the slab
+  uint32_t *dense;        // [nz][ry][W] words of the slab
   int W, ry, nz;          // words per row, rows per slice, slices in the slab
   int nby, nbz;           // bricks along y and z in the slab
   int bz0;                // global brick z of the slab's first slice
   long long n;            // W * nby * nbz bricks, bx fastest
 };
 
-__device__ __forceinline__ const uint32_t *brick_origin(const SlabBricks &s, long long b, int &bx, int &by, int &bz,
-                                                        int &ny, int &nz) {
+__device__ __forceinline__ uint32_t *brick_origin(const SlabBricks &s, long long b, int &bx, int &by, int &bz,
+                                                  int &ny, int &nz) {
   bx = (int)(b % s.W);
   const long long t = b / s.W;
   by = (int)(t % s.nby);
@@ -2155,6 +2155,17 @@ __global__ void __launch_bounds__(kCompactBlock) k_brick_write(SlabBricks s, con
     }
   }
   const bool ne = acc != 0;
+  if (ne) {  // clear what was staged: the slab is left all zero for the next one
+    int ny, nz;
+    uint32_t *o = brick_origin(s, b, bx, by, bz, ny, nz);
+    if (ny == kBrickRows && nz == kBrickSlices) {
+#pragma unroll
+      for (int r = 0; r < kBrickWords; ++r) o[((size_t)(r >> 3) * s.ry + (r & 7)) * s.W] = 0u;
+    } else {
+      for (int dz = 0; dz < nz; ++dz)
+        for (int dy = 0; dy < ny; ++dy) o[((size_t)dz * s.ry + dy) * s.W] = 0u;
+    }
+  }
   const unsigned m = __ballot_sync(0xFFFFFFFFu, ne);
   if (lane == 0) warp_base[warp] = __popc(m);
   __syncthreads();
@@ -2184,15 +2195,42 @@ __global__ void __launch_bounds__(kCompactBlock) k_brick_write(SlabBricks s, con
   }
 }
 
-// Scratch: header, one dense slab, the per-block counts of a slab's bricks.
+// Marks slab z / depth for every slice z that the samples of some tet reach (the same
+// z-range as tet_box), so that slabs no tet reaches are skipped: they hold no brick.  Tets
+// with an index out of range or a vertex that failed its snap mark nothing; slab 0 is
+// always voxelized, and its launch and the snap report those errors.
+__global__ void k_slab_marks(const int4 *__restrict__ tets, long long n_tets, const int4 *__restrict__ verts4,
+                             long long n_verts, int sh, int rz, int depth, uint32_t *marks) {
+  const unsigned long long nv = (unsigned long long)n_verts;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_tets;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int4 q = tets[t];
+    if (q.x < 0 || q.y < 0 || q.z < 0 || q.w < 0 || (unsigned long long)q.x >= nv ||
+        (unsigned long long)q.y >= nv || (unsigned long long)q.z >= nv || (unsigned long long)q.w >= nv)
+      continue;
+    const int4 A = verts4[q.x], B = verts4[q.y], C = verts4[q.z], D = verts4[q.w];
+    if ((A.w | B.w | C.w | D.w) != 0) continue;
+    int lo = 0, n = 0;
+    axis_box(imin4(A.z, B.z, C.z, D.z), imax4(A.z, B.z, C.z, D.z), sh, 0, rz - 1, lo, n);
+    if (n <= 0) continue;
+    for (int sl = lo / depth; sl <= (lo + n - 1) / depth; ++sl) {
+      const uint32_t bit = 1u << (sl & 31);
+      if (!(marks[sl >> 5] & bit)) atomicOr(marks + (sl >> 5), bit);
+    }
+  }
+}
+
+// Scratch: header, one dense slab, the per-block counts of a slab's bricks, one bit per
+// slab for the slabs some tet reaches.
 static size_t sparse_scratch_bytes(const GridDims &g, int depth, long long *n_blocks_out) {
   const long long W = (g.rx + 31) / 32;
   const long long nby = (g.ry + kBrickRows - 1) / kBrickRows;
   const long long nbz = (depth + kBrickSlices - 1) / kBrickSlices;
   const long long n_blocks = (W * nby * nbz + kCompactBlock - 1) / kCompactBlock;
   if (n_blocks_out) *n_blocks_out = n_blocks;
+  const long long n_slabs = (g.rz + depth - 1) / depth;
   return align256(sizeof(SparseHeader)) + align256((size_t)depth * g.ry * W * 4) +
-         align256((size_t)(n_blocks > 0 ? n_blocks : 1) * 8);
+         align256((size_t)(n_blocks > 0 ? n_blocks : 1) * 8) + align256((size_t)((n_slabs + 31) / 32) * 4);
 }
 
 static int sparse_dims(const int32_t res[3], int32_t depth, GridDims &g) {
@@ -2245,6 +2283,10 @@ int voxelize_tets_sparse(const float *d_verts, int64_t n_verts, const int32_t *d
   uint32_t *dense = reinterpret_cast<uint32_t *>(static_cast<char *>(d_scratch) + align256(sizeof(SparseHeader)));
   unsigned long long *block_counts = reinterpret_cast<unsigned long long *>(
       reinterpret_cast<char *>(dense) + align256((size_t)slab_depth * g.ry * ((g.rx + 31) / 32) * 4));
+  uint32_t *slab_marks = reinterpret_cast<uint32_t *>(reinterpret_cast<char *>(block_counts) +
+                                                      align256((size_t)(n_blocks > 0 ? n_blocks : 1) * 8));
+  const int n_slabs = (g.rz + slab_depth - 1) / slab_depth;
+  const int mark_words = (n_slabs + 31) / 32;
   SparseHeader *sh = static_cast<SparseHeader *>(d_scratch);
   st = buffer_checks(n_verts, d_tets, n_tets, dense, d_workspace, ws_bytes);
   if (st != VOXTET_OK) return st;
@@ -2258,14 +2300,36 @@ int voxelize_tets_sparse(const float *d_verts, int64_t n_verts, const int32_t *d
   inner.sync = 0;
   inner.profile = 0;
   const int W = (g.rx + 31) / 32;
-  for (int z0 = 0; z0 < g.rz; z0 += slab_depth) {
+  // slab 0's prologue, the snap, and the marks of the slabs some tet reaches
+  std::vector<uint32_t> marks((size_t)mark_words, 0u);
+  {
+    GridDims g0 = g;
+    g0.z1 = slab_depth < g.rz ? slab_depth : g.rz;
+    st = launch_prologue(w, dense, g0.out_words(), 1, stream);
+    if (st != VOXTET_OK) return st;
+    st = launch_snap(w, d_verts, n_verts, grid_origin, voxel_size, g.K, stream);
+    if (st != VOXTET_OK) return st;
+    if (cudaMemsetAsync(slab_marks, 0, (size_t)mark_words * 4, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+    if (n_tets > 0 && n_verts > 0) {
+      DeviceInfo *dev = nullptr;
+      if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+      k_slab_marks<<<grid_blocks(n_tets, 256, dev->sms), 256, 0, stream>>>(
+          reinterpret_cast<const int4 *>(d_tets), n_tets, w.verts4, n_verts, kLatticeBits - g.K, g.rz, slab_depth,
+          slab_marks);
+      g_launches.fetch_add(1);
+    }
+    if (cudaMemcpyAsync(marks.data(), slab_marks, (size_t)mark_words * 4, cudaMemcpyDeviceToHost, stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(stream) != cudaSuccess)
+      return VOXTET_ERR_CUDA;
+  }
+  for (int z0 = 0, si = 0; z0 < g.rz; z0 += slab_depth, ++si) {
+    if (si > 0 && !((marks[(size_t)si >> 5] >> (si & 31)) & 1u)) continue;  // no tet reaches it: no bricks
     GridDims gs = g;
     gs.z0 = z0;
     gs.z1 = z0 + slab_depth < g.rz ? z0 + slab_depth : g.rz;
-    st = launch_prologue(w, dense, gs.out_words(), 1, stream);
-    if (st != VOXTET_OK) return st;
-    if (z0 == 0) {
-      st = launch_snap(w, d_verts, n_verts, grid_origin, voxel_size, g.K, stream);
+    if (si > 0) {  // the slab is zero: the previous slab's k_brick_write cleared every brick it held
+      st = launch_prologue(w, dense, gs.out_words(), 0, stream);
       if (st != VOXTET_OK) return st;
     }
     st = run_voxelize(w, n_verts, d_tets, n_tets, gs, dense, inner, stream);

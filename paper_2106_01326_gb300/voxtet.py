@@ -287,8 +287,12 @@ def sparse_scratch_size(res3: Sequence[int], slab_depth: int) -> int:
     return int(load().voxtet_sparse_scratch_size(ctypes.byref(r3), int(slab_depth)))
 
 
-def default_slab_depth(res3: Sequence[int], budget_bytes: int = 2 << 30) -> int:
-    """Slices per pass so that one dense slab stays within ``budget_bytes`` (a multiple of 8)."""
+def default_slab_depth(res3: Sequence[int], budget_bytes: int = 128 << 20) -> int:
+    """Slices per pass so that one dense slab stays within ``budget_bytes`` (a multiple of 8).
+
+    The default keeps a slab about the size of GB300's 129 MB L2, so that zeroing it, the ORs into
+    it and the brick count and compaction that read it back mostly stay in L2 instead of HBM
+    (torus_73: 4096^3 13.8 -> 11.4 ms, 8192^3 100 -> 77 ms against 2 GiB slabs)."""
     rx, ry, rz = (int(x) for x in res3)
     per_slice = ry * ((rx + 31) // 32) * 4
     d = max(8, min(rz, budget_bytes // max(per_slice, 1)) // 8 * 8)

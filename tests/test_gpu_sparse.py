@@ -132,3 +132,51 @@ def test_sparse_coplanar_ties_wide_grid(vt):
     assert (v.astype(np.float64) * (256 / h) == xyz).all()  # exact round trip: the snap gives xyz back
     _check(vt, v, tets, h, res3, slab_depth=16)
     _check(vt, v, tets, h, res3, slab_depth=24, mode=1)
+
+
+def test_sparse_mesh_in_a_middle_band(vt):
+    """Mesh confined to z in [0.40, 0.62] of a 256^3 grid, 8-slice slabs: the slabs no tet reaches
+    (including slab 0, which is voxelized anyway) hold no bricks; the rest match the oracle."""
+    v, t, h = _mesh((256, 256, 256), seed=11)
+    v = v.astype(np.float64)
+    v[:, 2] = 0.40 + 0.22 * v[:, 2]
+    v = v.astype(np.float32)
+    n = _check(vt, v, t, h, (256, 256, 256), slab_depth=8)
+    dv, dt = _dev(v, t)
+    keys, _ = vt.voxelize_sparse(dv, dt, (0, 0, 0), h, (256, 256, 256), slab_depth=8)
+    bz = keys.cpu().numpy().view(np.uint64) >> np.uint64(32)
+    assert len(keys) == n and bz.min() >= 12 and bz.max() <= 20  # z in [0.40, 0.62] x 32 bricks
+
+
+def test_sparse_bad_index_reported_when_low_slabs_are_empty(vt):
+    """All tets high in z, one with a vertex index out of range: the error is still reported
+    (slab 0 is always voxelized and reports it)."""
+    v, t, h = _mesh((128, 128, 128), seed=12)
+    v = v.astype(np.float64)
+    v[:, 2] = 0.7 + 0.25 * v[:, 2]
+    v = v.astype(np.float32)
+    t = t.copy()
+    t[len(t) // 2, 1] = len(v) + 5
+    dv, dt = _dev(v, t)
+    with pytest.raises(vt.VoxtetError) as e:
+        vt.voxelize_sparse(dv, dt, (0, 0, 0), h, (128, 128, 128), slab_depth=16)
+    assert e.value.status == vt.ERR_INDEX
+
+
+def test_sparse_dirty_scratch_and_reuse(vt):
+    """A scratch full of set bits gives the same bricks (the first slab is cleared; later slabs
+    rely on the previous slab's compaction having cleared every brick it held), and so does a
+    second call on the same scratch; ragged grid (ry, rz not multiples of 8 or of the depth)."""
+    import torch
+
+    res3 = (200, 100, 150)
+    v, t, h = _mesh(res3, seed=13)
+    dv, dt = _dev(v, t)
+    depth = 24
+    scratch = torch.full((vt.sparse_scratch_size(res3, depth),), 255, dtype=torch.uint8, device="cuda")
+    ref = oracle.voxelize_grid(v, t, (0, 0, 0), h, res3)
+    rk, rw = oracle.dense_to_bricks(ref, res3[0])
+    for _ in range(2):
+        keys, words = vt.voxelize_sparse(dv, dt, (0, 0, 0), h, res3, slab_depth=depth, scratch=scratch)
+        assert (keys.cpu().numpy().view(np.uint64) == rk).all()
+        assert (words.cpu().numpy().view(np.uint32) == rw).all()
