@@ -1994,6 +1994,8 @@ constexpr int kBrickSlices = 8;                      // z slices per brick
 constexpr int kBrickWords = kBrickRows * kBrickSlices;
 constexpr int kCompactBlock = 128;
 
+constexpr int kSparseSpanRows = 64;  // default span size of the slab launches of the sparse path
+
 struct SparseHeader {
   unsigned long long total;  // non-empty bricks of all slabs so far (may exceed the capacity)
   int sticky_bits;           // device-detected status bits of every slab
@@ -2299,6 +2301,10 @@ int voxelize_tets_sparse(const float *d_verts, int64_t n_verts, const int32_t *d
   voxtet_opts inner = o;
   inner.sync = 0;
   inner.profile = 0;
+  // A slab launch holds only the tets that reach the slab, so it has far fewer spans than a
+  // whole-grid launch; spans of one slice (about 64 rows) keep the threads evenly busy
+  // (measured on GB300, torus_73 with 128 MiB slabs: 4096^3 6.6 -> 6.0 ms, 8192^3 38 -> 34 ms).
+  if (inner.span_rows == 0) inner.span_rows = kSparseSpanRows;
   const int W = (g.rx + 31) / 32;
   // slab 0's prologue, the snap, and the marks of the slabs some tet reaches
   std::vector<uint32_t> marks((size_t)mark_words, 0u);
