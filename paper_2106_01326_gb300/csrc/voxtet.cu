@@ -565,6 +565,7 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
   // walk the candidate rows slice by slice; moving to the next table entry is a short
   // straight-line step (no empty slices in the table)
   int m_tab = 0, b = 0, b_end = 0;
+  uint32_t e_next = tab[0][tid];  // the next table entry, loaded one slice ahead
   float bf = 0.f, ac[4];
   uint32_t *row = p.out;
   const float fhi0 = (float)(bx.na - 1);
@@ -574,8 +575,9 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
   const unsigned slice_words = (unsigned)p.ry * (unsigned)p.W;
   for (unsigned r = 0; r < total; ++r) {
     if (b == b_end) {
-      const uint32_t e = tab[m_tab][tid];
+      const uint32_t e = e_next;
       ++m_tab;
+      e_next = tab[m_tab < nt ? m_tab : nt - 1][tid];
       const int k = (int)(e & 31u);
       b = (int)((e >> 5) & 0x3FFFu);
       b_end = b + 1 + (int)(e >> 19);
@@ -640,7 +642,7 @@ constexpr int kBuckets = 32;
 struct TileSmem {
   uint32_t off[kTile + 1];
   uint32_t warp_tot[kBlock / 32];
-  uint16_t order[kSortedSpans];  // spans by estimated work
+  uint32_t order[kSortedSpans];  // spans by estimated work: tet slot << 16 | span within the tet
   uint32_t bucket[kBuckets];
   float wmin, wmax;
   RowStage stage;
@@ -758,27 +760,36 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
     for (int k = 0; k < kPerThread; ++k) {
       if (cnt[k]) {
         const uint32_t pos = atomicAdd(&sm.bucket[bk[k]], cnt[k]);
-        const uint32_t first = sm.off[tid * kPerThread + k];
-        for (uint32_t q = 0; q < cnt[k]; ++q) sm.order[pos + q] = (uint16_t)(first + q);
+        // span q of the tet in slot u is stored as u << 16 | q (q < 2^16: a tet spans at most 65536 slices)
+        for (uint32_t q = 0; q < cnt[k]; ++q) sm.order[pos + q] = ((uint32_t)(tid * kPerThread + k) << 16) | q;
       }
     }
     __syncthreads();
   }
 
-  // (3)+(4) spans (by estimated work when sorted); the tet slot of span sp is the
-  // largest u with off[u] <= sp
+  // (3)+(4) spans, by estimated work when sorted (the sort recorded each span's tet slot
+  // and its index within the tet); unsorted, span i belongs to the largest slot u with
+  // off[u] <= i
   // Rounds of kBlock spans, dealt forwards and backwards in turn: each warp still gets 32
   // neighbouring spans of the work order, and no thread takes the largest of every round
   // (the block waits at the tile's end for its slowest thread).
   for (uint32_t r0 = 0; r0 < total; r0 += kBlock) {
     const uint32_t i = r0 + (((r0 / kBlock) & 1u) ? (uint32_t)(kBlock - 1 - tid) : (uint32_t)tid);
     if (i >= total) continue;
-    const uint32_t sp = sorted ? (uint32_t)sm.order[i] : i;
-    int a = 0, bnd = kTile - 1;
-    while (a < bnd) {
-      const int mid = (a + bnd + 1) >> 1;
-      if (sm.off[mid] <= sp) a = mid;
-      else bnd = mid - 1;
+    int a = 0;
+    uint32_t q = 0;
+    if (sorted) {
+      const uint32_t o = sm.order[i];
+      a = (int)(o >> 16);
+      q = o & 0xFFFFu;
+    } else {
+      int bnd = kTile - 1;
+      while (a < bnd) {
+        const int mid = (a + bnd + 1) >> 1;
+        if (sm.off[mid] <= i) a = mid;
+        else bnd = mid - 1;
+      }
+      q = i - sm.off[a];
     }
     const long long t = tile_tet<STRIDED>(p, base, a);
     int3 V[4];
@@ -787,7 +798,7 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
     load_tet(p, t, V, dummy);
     tet_box(V, p.sh, p.rx, p.ry, p.z0, p.z1, bx);
     const int S = slices_per_span(p, bx.nb, bx.nc);
-    const int c0 = (int)(sp - sm.off[a]) * S;
+    const int c0 = (int)q * S;
     ctr.rows += run_span<STRICT, CULL, CLAMP>(p, t, V, bx, c0, min(c0 + S, bx.nc), slice_tab, sm.stage);
   }
   flush_stage(p, sm.stage);
