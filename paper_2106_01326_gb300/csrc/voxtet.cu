@@ -269,14 +269,16 @@ __device__ __forceinline__ int slices_per_span(const Params &p, int nb, int nc) 
 }
 
 // Phase (1): classify tet t and return its span count for the filter path (0 if it
-// marks nothing or was queued for the exact kernel).
+// marks nothing or was queued for the exact kernel); `meta` gets the orientation flag and
+// the slices per span, which the span phase reuses.
 __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, int &err, unsigned &n_degenerate,
-                                                 unsigned &n_wide, float &work) {
+                                                 unsigned &n_wide, float &work, uint32_t &meta) {
   int3 V[4];
   if (!load_tet(p, t, V, err)) return 0;
   Box bx;
   const int E = tet_box(V, p.sh, p.rx, p.ry, p.z0, p.z1, bx);
-  if (v6_sign(V, E) == 0) {
+  const int sg = v6_sign(V, E);
+  if (sg == 0) {
     ++n_degenerate;
     return 0;
   }
@@ -302,6 +304,7 @@ __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, i
     const float inv = __int_as_float((127 - 2 * p.sh) << 23);  // 1 / (2s)^2, an exact power of two
     work = (fabsf(n1x) + fabsf(n2x) + fabsf(n3x) + fabsf(n1x + n2x + n3x)) * 0.25f * inv + (float)bx.nc;
   }
+  meta = (uint32_t)(sg < 0) | ((uint32_t)S << 1);
   return (uint32_t)((bx.nc + S - 1) / S);
 }
 
@@ -464,15 +467,15 @@ constexpr int kMaxSlicesPerSpan = 32;
 constexpr size_t kSliceTableBytesMax = (size_t)kMaxSlicesPerSpan * kBlock * sizeof(uint32_t);
 static size_t slice_table_bytes(int max_slices) { return (size_t)max_slices * kBlock * sizeof(uint32_t); }
 
-// Phases (3)+(4): slices [c0, c1) (at most kMaxSlicesPerSpan) of a narrow tet whose
-// four faces all depend on x.  First the candidate rows of every slice are found and
-// written to this thread's column of `tab` (b_lo | count << 16), then one flat loop
-// walks all candidate rows, so the lanes of a warp stay in step across slices.
-// Returns the rows visited.
+// Phases (3)+(4): slices [c0, c1) (at most kMaxSlicesPerSpan) of a narrow tet, whose
+// vertices V2 and V3 are swapped first when `flip` (the classification found V6 < 0).
+// First the candidate rows of every slice are found and the non-empty slices written to
+// this thread's column of `tab`, then one flat loop walks all candidate rows, so the
+// lanes of a warp stay in step across slices.  Returns the rows visited.
 template <bool STRICT, bool CULL, bool CLAMP>
 __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 V[4], const Box &bx, int c0, int c1,
-                                             uint32_t (*tab)[kBlock], RowStage &stage) {
-  if (v6_sign(V, kNarrowExtent) < 0) {  // orient (the tet is narrow: 64-bit sign)
+                                             uint32_t (*tab)[kBlock], RowStage &stage, bool flip) {
+  if (flip) {  // orient (classification found V6 < 0)
     const int3 tmp = V[2];
     V[2] = V[3];
     V[3] = tmp;
@@ -643,6 +646,7 @@ struct TileSmem {
   uint32_t off[kTile + 1];
   uint32_t warp_tot[kBlock / 32];
   uint32_t order[kSortedSpans];  // spans by estimated work: tet slot << 16 | span within the tet
+  uint8_t meta[kTile];           // per tet slot: 1 if V6 < 0 (swap V2, V3) | slices per span << 1
   uint32_t bucket[kBuckets];
   float wmin, wmax;
   RowStage stage;
@@ -678,7 +682,9 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
   for (int k = 0; k < kPerThread; ++k) {
     const long long t = tile_tet<STRIDED>(p, base, (long long)tid * kPerThread + k);
     work[k] = 0.f;
-    cnt[k] = t < end ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide, work[k]) : 0u;
+    uint32_t mt = 0;
+    cnt[k] = t < end ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide, work[k], mt) : 0u;
+    sm.meta[tid * kPerThread + k] = (uint8_t)mt;
     if (cnt[k]) {
       work[k] /= (float)cnt[k];  // per span
       wlo = fminf(wlo, work[k]);
@@ -797,9 +803,10 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
     int dummy = 0;
     load_tet(p, t, V, dummy);
     tet_box(V, p.sh, p.rx, p.ry, p.z0, p.z1, bx);
-    const int S = slices_per_span(p, bx.nb, bx.nc);
+    const uint32_t mt = sm.meta[a];
+    const int S = (int)(mt >> 1);
     const int c0 = (int)q * S;
-    ctr.rows += run_span<STRICT, CULL, CLAMP>(p, t, V, bx, c0, min(c0 + S, bx.nc), slice_tab, sm.stage);
+    ctr.rows += run_span<STRICT, CULL, CLAMP>(p, t, V, bx, c0, min(c0 + S, bx.nc), slice_tab, sm.stage, (mt & 1u) != 0);
   }
   flush_stage(p, sm.stage);
 }
