@@ -103,9 +103,9 @@ def recorded_traffic(workload: str):
         return None
 
 
-# Algorithmic ALU work per unit (mid-points of the per-unit estimates of the design
-# survey): 25 lane-ops per candidate x-row (four affine bounds, their rounding and
-# certification, the word mask) and 150 per tetrahedron (box, orientation, face data).
+# Algorithmic ALU work per unit: 25 lane-ops per candidate x-row (four affine bounds, their
+# rounding and certification, the word mask) and 150 per tetrahedron (box, orientation,
+# face data), the minimum counts of the operations the method needs per unit.
 ALU_OPS_PER_ROW = 25
 ALU_OPS_PER_TET = 150
 
