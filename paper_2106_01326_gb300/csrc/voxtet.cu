@@ -480,6 +480,29 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
     V[2] = V[3];
     V[3] = tmp;
   }
+  const int tid = threadIdx.x;
+  const int ns = c1 - c0;
+  // slice table: only slices with candidate rows, packed k | b_lo << 5 | (n - 1) << 19
+  // (k < 32 slices, b_lo < 2^14, n <= 8192 rows).  Built before the face data so that the
+  // edge lines and the face data are never live together.
+  unsigned total = 0;
+  int nt = 0;
+  {
+    EdgeLines EL;
+    if (CULL) edge_lines(V, EL);
+    const int s = 1 << (p.sh - 1);
+    for (int k = 0; k < ns; ++k) {
+      int b_lo = 0, b_hi = bx.nb - 1;
+      if (CULL) slice_rows_sorted(EL, s + ((bx.l0 + c0 + k) << p.sh), s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
+      if (b_hi >= b_lo) {
+        const int n = b_hi - b_lo + 1;
+        tab[nt][tid] = (uint32_t)k | ((uint32_t)b_lo << 5) | ((uint32_t)(n - 1) << 19);
+        ++nt;
+        total += (unsigned)n;
+      }
+    }
+  }
+  if (total == 0) return 0;
   // Filter data per face, built one face at a time; faces parallel to x (at most
   // two) become neutral upper bounds here and exact row conditions below.
   float al[4], be[4], ga[4], de[4];
@@ -513,6 +536,26 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
     VOXTET_SLOT(3)
 #undef VOXTET_SLOT
   }
+  if (nz > 0) {  // faces parallel to x: exact row conditions narrow the table's entries
+    int nt2 = 0;
+    total = 0;
+    for (int m = 0; m < nt; ++m) {
+      const uint32_t e = tab[m][tid];
+      const int k = (int)(e & 31u);
+      int b_lo = (int)((e >> 5) & 0x3FFFu);
+      int b_hi = b_lo + (int)(e >> 19);
+      narrow_by_row_constraint<STRICT>(zL0 + zDz0 * (i64)(c0 + k), zDy0, b_lo, b_hi);
+      if (nz > 1) narrow_by_row_constraint<STRICT>(zL1 + zDz1 * (i64)(c0 + k), zDy1, b_lo, b_hi);
+      if (b_hi >= b_lo) {
+        const int n = b_hi - b_lo + 1;
+        tab[nt2][tid] = (uint32_t)k | ((uint32_t)b_lo << 5) | ((uint32_t)(n - 1) << 19);
+        ++nt2;
+        total += (unsigned)n;
+      }
+    }
+    nt = nt2;
+    if (total == 0) return 0;
+  }
   // Order the faces upper bounds first.  Every live tet has at least one face with
   // Dx < 0 and one with Dx > 0 (the four gradients sum to zero and at most two are
   // zero), so slot 0 is always an upper bound and slot 3 a lower bound; only slots 1
@@ -540,30 +583,6 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
     up1 = nup >= 2;
     up2 = nup >= 3;
   }
-  const int tid = threadIdx.x;
-  const int ns = c1 - c0;
-  // slice table: only slices with candidate rows, packed k | b_lo << 5 | (n - 1) << 19
-  // (k < 32 slices, b_lo < 2^14, n <= 8192 rows)
-  unsigned total = 0;
-  int nt = 0;
-  {
-    EdgeLines EL;
-    if (CULL) edge_lines(V, EL);
-    const int s = 1 << (p.sh - 1);
-    for (int k = 0; k < ns; ++k) {
-      int b_lo = 0, b_hi = bx.nb - 1;
-      if (CULL) slice_rows_sorted(EL, s + ((bx.l0 + c0 + k) << p.sh), s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
-      if (nz > 0) narrow_by_row_constraint<STRICT>(zL0 + zDz0 * (i64)(c0 + k), zDy0, b_lo, b_hi);
-      if (nz > 1) narrow_by_row_constraint<STRICT>(zL1 + zDz1 * (i64)(c0 + k), zDy1, b_lo, b_hi);
-      if (b_hi >= b_lo) {
-        const int n = b_hi - b_lo + 1;
-        tab[nt][tid] = (uint32_t)k | ((uint32_t)b_lo << 5) | ((uint32_t)(n - 1) << 19);
-        ++nt;
-        total += (unsigned)n;
-      }
-    }
-  }
-  if (total == 0) return 0;
 
   // walk the candidate rows slice by slice; moving to the next table entry is a short
   // straight-line step (no empty slices in the table)
