@@ -76,7 +76,7 @@ typedef struct {
     int32_t span_rows;  /* bounding-box x-rows per work item (whole z-slices, at most 16 of them, 32 when the
                            grid's longest side is 1024 or more); 0 = automatic (256, 1024 for grids whose
                            longest side is in [1024, 2048), 64 for the slabs of voxelize_tets_sparse) */
-    int32_t block;      /* threads per block of the scanline kernel; 0 = automatic (only 256 is accepted) */
+    int32_t block;      /* threads per block of the scanline kernel; 0 = automatic (only 128 is accepted) */
     int32_t profile;    /* 1 = record CUDA events around the main kernel on `stream` (see voxtet_stats) */
     int32_t row_cull;   /* skip x-rows outside each z-slice's cross-section: 0 = automatic, 1 = on, 2 = off */
 } voxtet_opts;

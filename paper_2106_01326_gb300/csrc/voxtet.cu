@@ -46,10 +46,13 @@
 namespace voxtet {
 
 #ifndef VOXTET_MIN_BLOCKS
-#define VOXTET_MIN_BLOCKS 3  // resident blocks per SM the register budget is sized for
+#define VOXTET_MIN_BLOCKS 6  // resident blocks per SM the register budget is sized for
 #endif
 
-constexpr int kBlock = 256;             // threads per block
+// Threads per block.  128-thread blocks of 512-tet tiles, 6 per SM, wait less at the tile
+// barriers than 256-thread blocks of 1024-tet tiles, 3 per SM (measured on GB300: sliver
+// mesh 512^3 kernel 336 -> 330 us, 1024^3 1117 -> 1088 us; torus 48^3 at 256^3 26.2 -> 24.1 us).
+constexpr int kBlock = 128;
 // Bounding-box rows per span (whole z-slices) when the caller does not choose (the
 // autotuner picks per mesh).  Measured on GB300 with the sliver and torus meshes: 256 is
 // best or within 13 % of it at every size except 1024^3, where 1024 (with 32-slice
@@ -654,11 +657,11 @@ __device__ __forceinline__ unsigned run_span(const Params &p, long long t, int3 
 
 // ------------------------------------------------------------------ the fused kernel
 
-constexpr int kTile = 1024;      // tets per tile
-constexpr int kSmallTile = 256;  // tets per tile at the end of a single-mesh launch
+constexpr int kTile = 512;      // tets per tile
+constexpr int kSmallTile = 128;  // tets per tile at the end of a single-mesh launch
 constexpr int kPerThread = kTile / kBlock;
 
-constexpr int kSortedSpans = 4096;  // tiles with more spans run in their natural order
+constexpr int kSortedSpans = 2048;  // tiles with more spans run in their natural order
 constexpr int kBuckets = 32;
 
 struct TileSmem {
