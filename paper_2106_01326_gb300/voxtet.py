@@ -295,8 +295,10 @@ def default_slab_depth(res3: Sequence[int], budget_bytes: int = 128 << 20) -> in
     (torus_73: 4096^3 13.8 -> 11.4 ms, 8192^3 100 -> 77 ms against 2 GiB slabs)."""
     rx, ry, rz = (int(x) for x in res3)
     per_slice = ry * ((rx + 31) // 32) * 4
-    d = max(8, min(rz, budget_bytes // max(per_slice, 1)) // 8 * 8)
-    return min(d, (rz + 7) // 8 * 8)
+    fit = budget_bytes // max(per_slice, 1)
+    if fit >= rz:  # the whole grid in one slab (rounded up: the last slab is cut at rz)
+        return (rz + 7) // 8 * 8
+    return max(8, fit // 8 * 8)
 
 
 def voxelize_sparse(verts, tets, origin: Sequence[float], voxel_size: float, res3: Sequence[int],

@@ -103,3 +103,28 @@ def test_grid_argument_checks_before_launch(lib):
     assert call(z0=3, z1=3, out=0, h=-1.0) == vt.ERR_ARG  # NULL output allowed for an empty slab only
     assert call(h=-1.0) == vt.ERR_ARG
     assert call(wsb=ws - 1) == vt.ERR_WORKSPACE
+
+
+def test_sparse_host_sizing(lib):
+    """Slab depth defaults and scratch sizes of the brick-sparse path (no launch)."""
+    dsd = vt.default_slab_depth
+    assert dsd((256, 256, 256)) == 256  # 8 MiB grid: one slab
+    assert dsd((300, 100, 150)) == 152  # fits: one slab, rounded up to whole bricks
+    assert dsd((4096, 4096, 4096)) == 64  # 2 MiB per slice: 128 MiB slabs
+    assert dsd((8192, 8192, 8192)) == 16
+    assert dsd((65536, 65536, 64)) == 8  # 512 MiB per slice: the minimum depth
+    for r3 in [(1, 1, 1), (33, 17, 9), (4096, 100, 5000), (65536, 32, 40)]:
+        d = dsd(r3)
+        assert d % 8 == 0 and d >= 8
+        per_slice = r3[1] * ((r3[0] + 31) // 32) * 4
+        assert d * per_slice <= 128 << 20 or d == 8 or d >= r3[2]
+    # scratch = 256 B header + the dense slab + block counts + slab marks, each 256-byte aligned
+    r3 = (256, 256, 256)
+    slab = 64 * 256 * 8 * 4
+    assert vt.sparse_scratch_size(r3, 64) >= 256 + slab
+    assert vt.sparse_scratch_size(r3, 64) % 256 == 0
+    assert vt.sparse_scratch_size(r3, 128) > vt.sparse_scratch_size(r3, 64)
+    assert vt.sparse_scratch_size(r3, 12) == 0  # not a multiple of 8
+    assert vt.sparse_scratch_size(r3, 0) == 0
+    assert vt.sparse_scratch_size((vt.SPARSE_MAX_SIDE + 1, 8, 8), 8) == 0
+    assert vt.sparse_scratch_size((0, 8, 8), 8) == 0
