@@ -128,3 +128,30 @@ def test_sparse_host_sizing(lib):
     assert vt.sparse_scratch_size(r3, 0) == 0
     assert vt.sparse_scratch_size((vt.SPARSE_MAX_SIDE + 1, 8, 8), 8) == 0
     assert vt.sparse_scratch_size((0, 8, 8), 8) == 0
+
+
+def test_batch_workspace_sizing(lib):
+    """voxtet_batch_workspace_size on jobs with fake device pointers (sizing never touches them)."""
+    P = 1 << 20
+
+    def jobs(sizes):
+        arr = (vt.Job * max(len(sizes), 1))()
+        for i, (nv, nt, res) in enumerate(sizes):
+            j = arr[i]
+            j.d_verts, j.n_verts, j.d_tets, j.n_tets = P, nv, P, nt
+            j.voxel_size, j.res, j.d_out_bits = 1.0 / res, res, P
+        return arr
+
+    sizes = [(100, 400, 32), (5000, 20000, 64), (10, 10, 128)]
+    a = jobs(sizes)
+    n = len(sizes)
+    total = lib.voxtet_batch_workspace_size(a, n, n)
+    assert total > 0 and total % 256 == 0
+    assert total >= sum(vt.workspace_size(nt, nv, res) for nv, nt, res in sizes)
+    assert lib.voxtet_batch_workspace_size(a, n, 4 * n) > total  # the table grows with max_jobs
+    assert lib.voxtet_batch_workspace_size(a, n, n - 1) == 0      # max_jobs < n_jobs
+    assert lib.voxtet_batch_workspace_size(a, -1, n) == 0
+    assert lib.voxtet_batch_workspace_size(None, n, n) == 0
+    bigger = jobs([(100, 400, 32), (5000, 80000, 64), (10, 10, 128)])
+    assert lib.voxtet_batch_workspace_size(bigger, n, n) > total
+    assert lib.voxtet_batch_workspace_size(jobs([]), 0, 1) > 0  # an empty batch still has its table
