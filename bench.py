@@ -122,7 +122,8 @@ def alu_roofline(rows: int, tets: int, kernel_ms: float) -> dict:
     ops = ALU_OPS_PER_ROW * rows + ALU_OPS_PER_TET * tets
     achieved = ops / (kernel_ms / 1000.0) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s", "frac": achieved / peak,
-            "algorithmic_ops": ops, "ops_per_row": ALU_OPS_PER_ROW, "ops_per_tet": ALU_OPS_PER_TET}
+            "algorithmic_ops": ops, "ops_per_row": ALU_OPS_PER_ROW, "ops_per_tet": ALU_OPS_PER_TET,
+            "peak_source": f"152 SMs x 128 lanes x {mhz:.0f} MHz"}
 
 
 def load_peaks():
@@ -672,10 +673,13 @@ def run_ours(args):
                 "single_call_value": whole_job_rate(n_t, jobs, args.steps, e2e_single_total),
                 "grids_equal_device_path": bool(pipe_ok) if e2e_total else None},
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": recorded_traffic(args.workload), "kernel": "k_voxelize", "kernel_ms": kmean,
-                     "algorithmic_bytes": alg_bytes, "peak_source": peak_kind},
-        "alu_roofline": alu_roofline(int(stats["rows"]), n_t, kmean),
+        # the kernel is bound by issued lane operations, not by HBM: its primary roofline is the
+        # ALU one; the HBM fraction (algorithmic bytes over the measured copy bandwidth) is kept beside it
+        "roofline": dict(alu_roofline(int(stats["rows"]), n_t, kmean), traffic=recorded_traffic(args.workload),
+                         kernel="k_voxelize", kernel_ms=kmean),
+        "hbm_roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                         "traffic": recorded_traffic(args.workload), "kernel": "k_voxelize", "kernel_ms": kmean,
+                         "algorithmic_bytes": alg_bytes, "peak_source": peak_kind},
         "stats": {"rows": int(stats["rows"]), "spans": int(stats["spans"]),
                   "fallback_rows": int(stats["fallback_rows"]), "degenerate_tets": int(stats["degenerate_tets"]),
                   "wide_tets": int(stats["wide_tets"])},
