@@ -95,7 +95,6 @@ def load(path: Optional[str] = None):
                                              i32, P, P, i64, ctypes.POINTER(i64), P, sz, P, sz,
                                              ctypes.POINTER(Opts), P]
         lib.voxelize_tets_sparse.restype = ctypes.c_int
-        lib.voxelize_tets_fixed.restype = ctypes.c_int
         lib.voxtet_last_status.argtypes = [P, P]
         lib.voxtet_last_status.restype = ctypes.c_int
         lib.voxtet_read_stats.argtypes = [P, ctypes.POINTER(Stats), P]
