@@ -698,9 +698,12 @@ def run_ours(args):
 
         oracle.build()
         v, dt, depth, cores = cpu_oracle_sample(cfg, args.slab)
+        v1, dt1, depth1, _ = cpu_oracle_sample(cfg, max(8, args.slab // 8), n_threads=1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": f"z-slab of {depth} of {res} slices, all tets overlapping it, {dt:.2f} s; "
                                           f"tets/s = n_tets x {depth}/{res} / time",
+                                "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                                  "sample": f"z-slab of {depth1} of {res} slices, {dt1:.2f} s"},
                                 "paper_cpu_method": paper_cpu_comparison(cfg)}
     print(json.dumps(line), flush=True)
     if dist is not None:
