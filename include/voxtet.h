@@ -172,13 +172,14 @@ int voxelize_tets_grid(const float *d_verts, int64_t n_verts, const int32_t *d_t
 #define VOXTET_BRICK_WORDS 64
 
 /* Bytes of device scratch voxelize_tets_sparse needs for this grid and slab depth
- * (256-byte aligned): a dense slab of slab_depth slices plus compaction counters.
- * 0 if the arguments are invalid. */
+ * (256-byte aligned): a dense slab of slab_depth slices, compaction counters and one
+ * bit per slab.  0 if the arguments are invalid. */
 size_t voxtet_sparse_scratch_size(const int32_t res[3], int32_t slab_depth);
 
 /* Voxelize into bricks.  The grid is built slab_depth slices at a time (a multiple
- * of 8, >= 8) in d_scratch and each slab is compacted; larger slabs mean fewer
- * passes over the tetrahedra.
+ * of 8, >= 8) in d_scratch and each slab is compacted; slabs that no tetrahedron
+ * reaches are skipped.  Larger slabs mean fewer passes over the tetrahedra; slabs
+ * of about the size of the GPU's L2 cache (128 MiB on GB300) are fastest.
  *   res            HOST int32[3], sides in [1, VOXTET_SPARSE_MAX_SIDE]
  *   d_brick_keys   DEVICE uint64 [max_bricks], 8-byte aligned
  *   d_brick_words  DEVICE uint32 [max_bricks][VOXTET_BRICK_WORDS], 4-byte aligned
