@@ -90,6 +90,8 @@ def _load():
             lib.voxtet_oracle_theorem1_dets.restype = None
             lib.voxtet_oracle_num_threads.argtypes = []
             lib.voxtet_oracle_num_threads.restype = ctypes.c_int
+            lib.voxtet_oracle_last_threads.argtypes = []
+            lib.voxtet_oracle_last_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -373,7 +375,13 @@ def theorem1_dets(A, B, C, D, P) -> Tuple[int, int, int, int]:
 
 
 def num_threads() -> int:
+    """Threads a call with n_threads = 0 uses (the OpenMP default; no call changes it)."""
     return int(_load().voxtet_oracle_num_threads())
+
+
+def last_threads() -> int:
+    """Team size the last voxelization (or paper-method) call actually ran with."""
+    return int(_load().voxtet_oracle_last_threads())
 
 
 def unpack(grid: np.ndarray, res: int) -> np.ndarray:

@@ -29,6 +29,28 @@
 #include <omp.h>
 #endif
 
+/* Team size of the last region (defined in voxtet_oracle.c, same library). */
+extern int voxtet_oracle_last_team;
+
+/* n_threads > 0: that many threads for this call's region; 0: the OpenMP default.  A
+ * num_threads clause, so the count never leaks into later calls. */
+static int pc_team_size(int32_t n_threads) {
+#ifdef _OPENMP
+    return n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+    (void)n_threads;
+    return 1;
+#endif
+}
+
+static void pc_note_team(void) {
+#ifdef _OPENMP
+    voxtet_oracle_last_team = omp_get_num_threads();
+#else
+    voxtet_oracle_last_team = 1;
+#endif
+}
+
 #define PC_OK 0
 #define PC_ERR_ARG (-1)
 #define PC_ERR_RES (-2)
@@ -79,12 +101,11 @@ int voxtet_paper_cpu(const int32_t *xyz, int64_t n_verts, const int32_t *tets, i
     const int64_t s = (int64_t)1 << (19 - k);
     const int64_t W = (res + 31) / 32;
     memset(out_bits, 0, (size_t)((int64_t)res * res * W) * sizeof(uint32_t));
-#ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#else
-    (void)n_threads;
-#endif
-#pragma omp parallel for schedule(dynamic, 64)
+#pragma omp parallel num_threads(pc_team_size(n_threads))
+    {
+#pragma omp single
+        pc_note_team();
+#pragma omp for schedule(dynamic, 64)
     for (int64_t t = 0; t < n_tets; ++t) {
         int64_t V[4][3];
         for (int m = 0; m < 4; ++m)
@@ -139,6 +160,7 @@ int voxtet_paper_cpu(const int32_t *xyz, int64_t n_verts, const int32_t *tets, i
                                           __ATOMIC_RELAXED);
                 }
     }
+    }
     return PC_OK;
 }
 
@@ -171,13 +193,12 @@ int voxtet_paper_cpu_disagreements(const int32_t *xyz, int64_t n_verts, const in
     int k = 0;
     while ((1 << k) != res) ++k;
     const int64_t s = (int64_t)1 << (19 - k);
-#ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#else
-    (void)n_threads;
-#endif
     int64_t c0 = 0, c1 = 0, c2 = 0, c3 = 0, c4 = 0, c5 = 0;
-#pragma omp parallel for schedule(dynamic, 64) reduction(+ : c0, c1, c2, c3, c4, c5)
+#pragma omp parallel num_threads(pc_team_size(n_threads)) reduction(+ : c0, c1, c2, c3, c4, c5)
+    {
+#pragma omp single
+        pc_note_team();
+#pragma omp for schedule(dynamic, 64)
     for (int64_t t = 0; t < n_tets; ++t) {
         int64_t V[4][3];
         for (int m = 0; m < 4; ++m)
@@ -229,6 +250,7 @@ int voxtet_paper_cpu_disagreements(const int32_t *xyz, int64_t n_verts, const in
                     c4 += sign_pattern(ds[0], ds[1], ds[2], ds[3], 0) != xc;
                     c5 += sign_pattern(ds[0], ds[1], ds[2], ds[3], 1) != xst;
                 }
+    }
     }
     counts[0] = c0;
     counts[1] = c1;

@@ -54,6 +54,29 @@
 
 typedef __int128 i128;
 
+/* Threads of one parallel region: n_threads > 0 asks for that many, 0 for the
+ * OpenMP default.  It is given to each region as a num_threads clause, so one
+ * call never changes the thread count of later calls.  The team size the last
+ * region actually ran with is kept for voxtet_oracle_last_threads(). */
+static int team_size(int32_t n_threads) {
+#ifdef _OPENMP
+    return n_threads > 0 ? n_threads : omp_get_max_threads();
+#else
+    (void)n_threads;
+    return 1;
+#endif
+}
+
+int voxtet_oracle_last_team = 0;  /* shared with paper_cpu.c (same library) */
+
+static void note_team(void) {
+#ifdef _OPENMP
+    voxtet_oracle_last_team = omp_get_num_threads();
+#else
+    voxtet_oracle_last_team = 1;
+#endif
+}
+
 /* status codes (numeric values are part of the documented interface) */
 #define OR_OK 0
 #define OR_ERR_ARG (-1)
@@ -219,9 +242,9 @@ static void sample_box(const int64_t V[4][3], int64_t s, const int32_t res[3], t
 }
 
 static void prepare(const int32_t *xyz, const int32_t *tets, int64_t n_tets, const int32_t res[3], int64_t s,
-                    int mode, tet_box *boxes, int64_t *n_degenerate) {
+                    int mode, int32_t n_threads, tet_box *boxes, int64_t *n_degenerate) {
     int64_t degenerate = 0;
-#pragma omp parallel for schedule(static) reduction(+ : degenerate)
+#pragma omp parallel for schedule(static) reduction(+ : degenerate) num_threads(team_size(n_threads))
     for (int64_t t = 0; t < n_tets; ++t) {
         int64_t V[4][3];
         for (int m = 0; m < 4; ++m) load_vertex(xyz, tets[4 * t + m], V[m]);
@@ -254,22 +277,21 @@ static int voxelize_core(const int32_t *xyz, int64_t n_verts, const int32_t *tet
     const int64_t W = (res[0] + 31) / 32;
     const int64_t n_words = (int64_t)(z1 - z0) * ry * W;
     memset(out_bits, 0, (size_t)(n_words > 0 ? n_words : 0) * sizeof(uint32_t));
-#ifdef _OPENMP
-    if (n_threads > 0) omp_set_num_threads(n_threads);
-#else
-    (void)n_threads;
-#endif
     tet_box *boxes = (tet_box *)malloc((size_t)(n_tets > 0 ? n_tets : 1) * sizeof(tet_box));
     if (!boxes) return OR_ERR_ARG;
     int64_t degenerate = 0;
-    prepare(xyz, tets, n_tets, res, s, mode, boxes, &degenerate);
+    prepare(xyz, tets, n_tets, res, s, mode, n_threads, boxes, &degenerate);
 
     const int64_t depth = z1 - z0;
     int64_t chunk = 1;
     while (chunk * 64 < depth) chunk *= 2; /* at most 64 z-chunks */
     const int64_t n_chunks = depth > 0 ? (depth + chunk - 1) / chunk : 0;
     int64_t tested = 0;
-#pragma omp parallel for schedule(dynamic, 1) reduction(+ : tested)
+#pragma omp parallel num_threads(team_size(n_threads)) reduction(+ : tested)
+    {
+#pragma omp single
+        note_team();
+#pragma omp for schedule(dynamic, 1)
     for (int64_t ch = 0; ch < n_chunks; ++ch) {
         const int64_t c0 = z0 + ch * chunk;
         const int64_t c1 = (c0 + chunk - 1 < z1 - 1) ? c0 + chunk - 1 : z1 - 1;
@@ -289,6 +311,7 @@ static int voxelize_core(const int32_t *xyz, int64_t n_verts, const int32_t *tet
                             out_bits[((l - z0) * ry + j) * W + (i >> 5)] |= (uint32_t)1u << (i & 31);
                     }
         }
+    }
     }
     free(boxes);
     if (stats) {
@@ -419,10 +442,8 @@ void voxtet_oracle_theorem1_dets(const int64_t A[3], const int64_t B[3], const i
     }
 }
 
-int voxtet_oracle_num_threads(void) {
-#ifdef _OPENMP
-    return omp_get_max_threads();
-#else
-    return 1;
-#endif
-}
+/* Threads a call with n_threads = 0 uses (the OpenMP default; no call changes it). */
+int voxtet_oracle_num_threads(void) { return team_size(0); }
+
+/* Team size of the last voxelization or paper-method region that ran. */
+int voxtet_oracle_last_threads(void) { return voxtet_oracle_last_team; }

@@ -227,6 +227,26 @@ def test_thread_count_does_not_change_grid(oracle_lib):
     assert (g1 == g4).all()
 
 
+def test_thread_count_of_one_call_does_not_leak(oracle_lib):
+    """A call with n_threads = 1 must not lower the team of later default calls (the
+    oracle and the paper's CPU method time themselves on all cores by default)."""
+    v, t = mg.kuhn_lattice(6, 0.25, 9)
+    st, xyz = oracle.snap(v, (0, 0, 0), 1 / 64, 64)
+    default = oracle.num_threads()
+    oracle.voxelize_fixed(xyz, t, 64, n_threads=1)
+    assert oracle.last_threads() == 1
+    assert oracle.num_threads() == default
+    oracle.voxelize_fixed(xyz, t, 64)
+    assert oracle.last_threads() == default
+    oracle.paper_cpu(xyz, t, 64, "float", n_threads=1)
+    assert oracle.last_threads() == 1
+    oracle.paper_cpu(xyz, t, 64, "double")
+    assert oracle.last_threads() == default
+    oracle.voxelize_fixed_slab(xyz, t, 64, 10, 20, n_threads=2)
+    assert oracle.last_threads() == 2
+    assert oracle.num_threads() == default
+
+
 # ------------------------------------------------------------- invariants
 
 def _jittered(N=4, res=32, seed=0, jitter=0.3):
