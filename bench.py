@@ -110,19 +110,25 @@ ALU_OPS_PER_ROW = 25
 ALU_OPS_PER_TET = 150
 
 
-def alu_roofline(rows: int, tets: int, kernel_ms: float) -> dict:
+def alu_roofline(rows: int, tets: int, kernel_ms: float, rows_with_samples=None) -> dict:
     """The main kernel against the FP32/INT32 lane throughput (152 SMs x 128 lanes x
-    the maximum SM clock), the bound that actually limits it."""
+    the maximum SM clock), the bound that actually limits it.  The per-row work is counted
+    on the rows that hold a sample when that count is known (the oracle counts them: no
+    method can do less), else on the candidate rows the kernel visited (an upper bound)."""
     mhz = 2070.0
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
         with open(p) as f:
             mhz = float(json.load(f).get("sm_max_mhz", mhz))
     peak = 152 * 128 * mhz * 1e6 / 1e12
-    ops = ALU_OPS_PER_ROW * rows + ALU_OPS_PER_TET * tets
+    unit_rows = rows if rows_with_samples is None else int(rows_with_samples)
+    ops = ALU_OPS_PER_ROW * unit_rows + ALU_OPS_PER_TET * tets
     achieved = ops / (kernel_ms / 1000.0) / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tlane-op/s", "frac": achieved / peak,
             "algorithmic_ops": ops, "ops_per_row": ALU_OPS_PER_ROW, "ops_per_tet": ALU_OPS_PER_TET,
+            "rows_counted": "rows holding a sample (oracle)" if rows_with_samples is not None
+            else "candidate rows visited (kernel)", "rows_candidate": int(rows),
+            "rows_with_samples": None if rows_with_samples is None else int(rows_with_samples),
             "peak_source": f"152 SMs x 128 lanes x {mhz:.0f} MHz"}
 
 
@@ -204,24 +210,35 @@ def cpu_oracle_sample(cfg, slab, n_threads=0):
     return value, dt, (z1 - z0), oracle.num_threads() if n_threads <= 0 else n_threads
 
 
-def paper_cpu_comparison(cfg):
-    """The paper's CPU method in float and double (oracle/paper_cpu.c) on the same snapped mesh:
-    whole-grid mismatches against the exact oracle, per-test sign disagreements on the middle
-    128 slices, and the same on a tie-heavy soup (faces on planes through samples)."""
+def oracle_whole_grid(cfg):
+    """The oracle's grid of the whole workload (all host cores), with its time, the threads it
+    ran with and its counts (rows holding a sample: the per-row work the method cannot avoid)."""
     import oracle
-    from paper_2106_01326_gb300 import meshgen as mg
 
     res = cfg["res"]
     st, xyz = oracle.snap(cfg["verts"], cfg["origin"], cfg["voxel_size"], res)
     assert st == 0
-    out = {"what": "Theorem 1 in binary floating point on the oracle's snapped inputs (not exact)"}
     t0 = time.perf_counter()
-    exact = oracle.voxelize_fixed(xyz, cfg["tets"], res)
-    out["exact_oracle_s"] = time.perf_counter() - t0
+    exact, stats = oracle.voxelize_fixed(xyz, cfg["tets"], res, with_stats=True)
+    return exact, xyz, {"s": time.perf_counter() - t0, "threads": oracle.last_threads(), **stats}
+
+
+def paper_cpu_comparison(cfg, exact, xyz, exact_info):
+    """The paper's CPU method in float and double (oracle/paper_cpu.c) on the same snapped mesh:
+    whole-grid mismatches against the exact oracle, per-test sign disagreements on the middle
+    128 slices, and the same on a tie-heavy soup (faces on planes through samples).  Every time
+    carries the threads it ran with."""
+    import oracle
+    from paper_2106_01326_gb300 import meshgen as mg
+
+    res = cfg["res"]
+    out = {"what": "Theorem 1 in binary floating point on the oracle's snapped inputs (not exact)",
+           "exact_oracle_s": exact_info["s"], "exact_oracle_threads": exact_info["threads"]}
     for prec in ("float", "double"):
         t0 = time.perf_counter()
         g = oracle.paper_cpu(xyz, cfg["tets"], res, prec, 0)
         out[f"{prec}_s"] = time.perf_counter() - t0
+        out[f"{prec}_threads"] = oracle.last_threads()
         extra, missing = oracle.mismatches(g, exact)
         out[f"{prec}_grid_mismatches"] = {"extra": extra, "missing": missing}
     z0 = max(0, res // 2 - 64)
@@ -332,8 +349,12 @@ def batched_section(args, flush, stream):
     q = lambda xs, f: float(np.percentile(np.asarray(xs), f))
     return {
         "workload": f"256 meshes, {n_tets} tets (log-uniform 1k-100k per mesh), grids 32^3/64^3/128^3",
+        # every job of a replay is submitted with it and its grid is final when the replay's last
+        # kernel (the exact one, which serves all jobs) ends: each job's latency is its replay's
+        # duration, measured per replay
         "batched": {"jobs_per_s": len(specs) / (bmean / 1e3), "tets_per_s": n_tets / (bmean / 1e3),
-                    "ms_per_batch": bmean, "latency_ms_p50": bmean, "latency_ms_p99": bmean,
+                    "ms_per_batch": bmean, "latency_ms_p50": q(b_ms, 50), "latency_ms_p99": q(b_ms, 99),
+                    "latency_samples": len(b_ms) * len(specs),
                     "launches_per_batch": int(launches_batch), "form": "one CUDA-graph replay"},
         "per_mesh": {"jobs_per_s": len(specs) / (smean / 1e3), "tets_per_s": n_tets / (smean / 1e3),
                      "ms_per_batch": smean, "latency_ms_p50": q(s_lat, 50), "latency_ms_p99": q(s_lat, 99),
@@ -432,12 +453,14 @@ def slab_section(verts, tets, cfg, span_rows, row_cull, stream):
         times, parts, n_sub = [], [], []
         for z0, z1 in slabs.slab_cuts(res, n, w):
             g = vt.alloc_grid_dims((res, res, res), (z0, z1))
-            # the rank's tets (chosen once per mesh on the host, not timed)
-            sub = torch.from_numpy(slabs.tets_for_slab(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"],
-                                                       z0, z1)).to(tets.device)
+            # the rank's tets and only the vertices they name (chosen once per mesh on the host, not
+            # timed), so the rank snaps its own vertices only
+            sv, st = slabs.slab_mesh(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"], z0, z1)
+            sub = torch.from_numpy(st).to(tets.device)
+            subv = torch.from_numpy(sv).to(tets.device)
             n_sub.append(int(sub.shape[0]))
-            times.append(timed(lambda g=g, z0=z0, z1=z1, sub=sub: vt.voxelize_grid(
-                verts, sub, cfg["origin"], cfg["voxel_size"], (res, res, res), z_range=(z0, z1), out=g,
+            times.append(timed(lambda g=g, z0=z0, z1=z1, sub=sub, subv=subv: vt.voxelize_grid(
+                subv, sub, cfg["origin"], cfg["voxel_size"], (res, res, res), z_range=(z0, z1), out=g,
                 workspace=ws, sync=False, span_rows=span_rows, row_cull=row_cull, stream=stream)))
             parts.append(g)
         same = bool(torch.equal(torch.cat(parts, dim=0), full))
@@ -458,7 +481,8 @@ def served_section(args):
     from paper_2106_01326_gb300 import meshgen as mg
     from paper_2106_01326_gb300 import voxtet as vt
 
-    pool = [batch.Mesh.from_numpy(v, t) for v, t in mg.mesh_pool(16, seed=1004, tets_lo=1000, tets_hi=2000000)]
+    host_pool = mg.mesh_pool(16, seed=1004, tets_lo=1000, tets_hi=2000000)
+    pool = [batch.Mesh.from_numpy(v, t) for v, t in host_pool]
     res_set = (64, 128, 256, 512)
     alone = {}
     checked = [0, 0]
@@ -487,9 +511,57 @@ def served_section(args):
     reqs = mg.poisson_stream(n, rate_per_s=rate, n_pool=len(pool), seed=1004, resolutions=res_set)
     rt = srv.serve(reqs, realtime=True).summary()
     srv.close()
+    verified = served_oracle_check(pool, host_pool, sat_reqs, res_set)
     return {"workload": f"{n} Poisson requests over 16 pooled meshes ({sum(m.n_tets for m in pool)} tets), "
                         f"grids {res_set}", "capacity": cap, "poisson_at_0.8_capacity": dict(rt, rate_per_s=rate),
-            "sampled_exact": f"{checked[1]}/{checked[0]}", "slots": 3, "arena_GiB": 4}
+            "sampled_exact": f"{checked[1]}/{checked[0]}", "sampled_oracle_exact": verified, "slots": 3,
+            "arena_GiB": 4}
+
+
+def served_oracle_check(pool, host_pool, reqs, res_set, n_check=400):
+    """The first ``n_check`` requests of the saturated stream plus the pool's largest mesh at the
+    finest grid and its smallest at the coarsest, served again (untimed) through the same
+    continuous-batching server, each result compared bit for bit with the oracle's grid."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2106_01326_gb300 import meshgen as mg
+    from paper_2106_01326_gb300 import server
+
+    oracle.build()
+    sizes = [len(t) for _, t in host_pool]
+    sub = list(reqs[:n_check])
+    last = sub[-1].arrival_s
+    sub.append(mg.Request(len(reqs), last, int(np.argmax(sizes)), max(res_set)))
+    sub.append(mg.Request(len(reqs) + 1, last, int(np.argmin(sizes)), min(res_set)))
+    ref = {}
+    t0 = time.perf_counter()
+    for r in sub:
+        key = (r.mesh_id, r.res)
+        if key not in ref:
+            v, t = host_pool[r.mesh_id]
+            g = oracle.voxelize(v, t, (0, 0, 0), 1.0 / r.res, r.res)
+            ref[key] = torch.from_numpy(g.view(np.int32)).cuda()
+    oracle_s = time.perf_counter() - t0
+    good = [0, 0]
+
+    def cmp(tk, grid):
+        good[0] += 1
+        good[1] += int(torch.equal(grid, ref[(tk.mesh_id, tk.res)]))
+
+    srv = server.Server(pool, arena_bytes=4 << 30, n_slots=3, slot_workspace_bytes=512 << 20, max_jobs=64,
+                        on_result=cmp)
+    try:
+        srv.serve(sub, realtime=False)
+    finally:
+        srv.close()
+    del ref
+    torch.cuda.empty_cache()
+    return {"exact": f"{good[1]}/{good[0]}", "requests": len(sub), "distinct_grids": len(set((r.mesh_id, r.res)
+                                                                                           for r in sub)),
+            "oracle_s": oracle_s, "oracle_threads": oracle.last_threads(),
+            "includes": "largest pool mesh at the finest grid, smallest at the coarsest"}
 
 
 def run_ours(args):
@@ -528,8 +600,9 @@ def run_ours(args):
         w = slabs.slice_weights(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"], res)
         z_range = slabs.rank_slab(res, rank, world, w)
         grid = vt.alloc_grid_dims((res, res, res), z_range, dev)
-        tets = torch.from_numpy(slabs.tets_for_slab(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"],
-                                                    *z_range)).to(dev)
+        sv, st = slabs.slab_mesh(cfg["verts"], cfg["tets"], cfg["origin"], cfg["voxel_size"], *z_range)
+        verts = torch.from_numpy(sv).to(dev)
+        tets = torch.from_numpy(st).to(dev)
     else:
         z_range = (0, res)
         grid = vt.alloc_grid(res, dev)
@@ -593,7 +666,7 @@ def run_ours(args):
         raise vt.VoxtetError(st)
 
     # end to end through the public API: pinned host mesh -> device, voxelize, grid -> pinned host
-    h_verts = torch.from_numpy(cfg["verts"]).pin_memory()
+    h_verts = verts.cpu().pin_memory()  # this rank's vertices (a slab's own under --partition slab)
     h_tets = tets.cpu().pin_memory()  # this rank's tets (a slab's subset under --partition slab)
     h_grid = torch.empty(grid.shape, dtype=torch.int32).pin_memory()
     d_verts = torch.empty_like(verts)
@@ -694,6 +767,8 @@ def run_ours(args):
     if not args.no_slabs and world == 1:
         line["slabs_one_gpu"] = slab_section(verts, tets, cfg, span_rows, row_cull, stream)
     if not args.no_cpu_baseline:
+        import numpy as np
+
         import oracle
 
         oracle.build()
@@ -703,8 +778,19 @@ def run_ours(args):
                                 "sample": f"z-slab of {depth} of {res} slices, all tets overlapping it, {dt:.2f} s; "
                                           f"tets/s = n_tets x {depth}/{res} / time",
                                 "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
-                                                  "sample": f"z-slab of {depth1} of {res} slices, {dt1:.2f} s"},
-                                "paper_cpu_method": paper_cpu_comparison(cfg)}
+                                                  "sample": f"z-slab of {depth1} of {res} slices, {dt1:.2f} s"}}
+        if not slab:
+            # the timed grid against the oracle's, every sample of it
+            exact, xyz, info = oracle_whole_grid(cfg)
+            got = grid.cpu().numpy().view(np.uint32).reshape(exact.shape)
+            line["parity"] = {"bit_identical_to_oracle": bool(np.array_equal(got, exact)),
+                              "compared": f"whole {res}^3 grid of the timed call ({res ** 3} samples)",
+                              "oracle_s": info["s"], "oracle_threads": info["threads"]}
+            # the per-row work the method cannot avoid: rows holding a sample (a property of the mesh
+            # and grid, counted by the oracle), beside the candidate rows the kernel visited
+            line["roofline"] = dict(line["roofline"], **alu_roofline(int(stats["rows"]), n_t, kmean,
+                                                                     rows_with_samples=info["rows_with_samples"]))
+            line["cpu_baseline"]["paper_cpu_method"] = paper_cpu_comparison(cfg, exact, xyz, info)
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

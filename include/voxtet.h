@@ -273,29 +273,44 @@ void voxtet_plan_destroy(voxtet_plan *plan);
 #define VOXTET_NOALLOC_SCRATCH_BYTES (16u << 20)
 
 /* voxelize_tets without a workspace argument, for callers that cannot allocate
- * device memory when they call: for example code running while a stream capture
- * is in progress (cudaMalloc may not be called then), plugins whose host
- * application owns the whole device-memory budget, or latency-critical loops that
- * must not enter an allocator.  (The paper has no counterpart; this is an
+ * device memory when they call: a plugin or library running inside a host
+ * application that owns the whole device-memory budget (a renderer or simulation
+ * that reserves the device's memory up front and hands out only its own buffers),
+ * or a latency-critical loop that must not enter cudaMalloc, which can synchronize
+ * the device and take milliseconds.  (The paper has no counterpart; this is an
  * interface convenience.)
  *
  * The workspace is a fixed array of VOXTET_NOALLOC_SCRATCH_BYTES compiled into
  * the library: every GPU that loads the library holds it until the process exits.
- * Meshes whose voxtet_workspace_size(n_tets, n_verts, res) exceeds it are rejected
- * with VOXTET_ERR_NOMEM before anything is launched (about 1M tetrahedra with
- * 200k vertices fit).  The function itself calls no allocator; opts->profile is
- * ignored.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current), so make that first call
- * before any stream capture.
+ * The minimum (grid-independent) workspace, voxtet_workspace_size(n_tets, n_verts,
+ * res) with any res <= 512, must fit in it, else the call returns VOXTET_ERR_NOMEM
+ * before anything is launched (about 1M tetrahedra with 200k vertices fit); the
+ * queue of rows the filter could not certify then takes the rest of the array.  The
+ * function itself calls no allocator; opts->profile is ignored.  The first call on
+ * each device (this one or voxtet_noalloc_status_async) looks up the array's device
+ * address with cudaGetSymbolAddress, with that device current, so make that first
+ * call before any stream capture.
+ *
+ * With opts->sync = 1 the call synchronizes `stream` and returns the device-detected
+ * status, as voxelize_tets does.  With opts->sync = 0 it returns once the work is
+ * enqueued; read the device-detected status with voxtet_noalloc_status_async.
  *
  * All calls share the one array and it keeps the last call's contents; what must
- * start at zero is cleared by every call.  Calls that overlap on the GPU (on
- * different streams or host threads without ordering) race on it and give
- * undefined results.  Other arguments, ownership and status codes are those of
- * voxelize_tets. */
+ * start at zero (status header, redo bitmap) is cleared by every call.  Calls that
+ * overlap on the GPU (on different streams or host threads without ordering) race on
+ * it and give undefined results.  Other arguments, ownership and status codes are
+ * those of voxelize_tets. */
 int voxelize_tets_noalloc(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
                           const float grid_origin[3], float voxel_size, int32_t res, uint32_t *d_out_bits,
                           const voxtet_opts *opts, void *stream);
+
+/* voxtet_status_async for the fixed array behind voxelize_tets_noalloc: enqueue on
+ * `stream` a copy of the status word the last voxelize_tets_noalloc call left
+ * (4 bytes) into *status_word (pinned host or device memory), without
+ * synchronizing; once the stream has passed that point,
+ * voxtet_status_of_word(*status_word) is that call's device-detected status.
+ * Allocates nothing.  VOXTET_ERR_ARG if status_word is NULL. */
+int voxtet_noalloc_status_async(int32_t *status_word, void *stream);
 
 #ifdef __cplusplus
 }

@@ -127,7 +127,7 @@ def voxelize_fixed(xyz: np.ndarray, tets: np.ndarray, res: int, mode: int = 0, n
     t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
     W = (res + 31) // 32 if res > 0 else 1
     out = np.zeros(max(res, 1) * max(res, 1) * W, dtype=np.uint32)
-    stats = np.zeros(3, dtype=np.int64)
+    stats = np.zeros(4, dtype=np.int64)
     st = lib.voxtet_oracle_voxelize_fixed(_ptr(x), len(x), _ptr(t), len(t), int(res), int(mode),
                                           int(n_threads), _ptr(out), _ptr(stats))
     if st != OK:
@@ -136,7 +136,8 @@ def voxelize_fixed(xyz: np.ndarray, tets: np.ndarray, res: int, mode: int = 0, n
         return (st, None, None) if with_stats else (st, None)
     grid = out.reshape(res, res, W)
     if with_stats:
-        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2]),
+                      "rows_with_samples": int(stats[3])}
     return grid
 
 
@@ -148,14 +149,15 @@ def voxelize_fixed_slab(xyz: np.ndarray, tets: np.ndarray, res: int, z0: int, z1
     t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
     W = (res + 31) // 32
     out = np.zeros(max(z1 - z0, 1) * res * W, dtype=np.uint32)
-    stats = np.zeros(3, dtype=np.int64)
+    stats = np.zeros(4, dtype=np.int64)
     st = lib.voxtet_oracle_voxelize_fixed_slab(_ptr(x), len(x), _ptr(t), len(t), int(res), int(mode),
                                                int(n_threads), int(z0), int(z1), _ptr(out), _ptr(stats))
     if st != OK:
         raise OracleError(st)
     grid = out[: (z1 - z0) * res * W].reshape(z1 - z0, res, W)
     if with_stats:
-        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2]),
+                      "rows_with_samples": int(stats[3])}
     return grid
 
 
@@ -168,7 +170,7 @@ def voxelize(verts: np.ndarray, tets: np.ndarray, origin, voxel_size: float, res
     o = np.ascontiguousarray(np.asarray(origin, dtype=np.float32).reshape(3))
     W = (res + 31) // 32 if res > 0 else 1
     out = np.zeros(max(res, 1) * max(res, 1) * W, dtype=np.uint32)
-    stats = np.zeros(3, dtype=np.int64)
+    stats = np.zeros(4, dtype=np.int64)
     st = lib.voxtet_oracle_voxelize(_ptr(v), len(v), _ptr(t), len(t), _ptr(o), float(voxel_size), int(res),
                                     int(mode), int(n_threads), _ptr(out), _ptr(stats))
     if st != OK:
@@ -177,7 +179,8 @@ def voxelize(verts: np.ndarray, tets: np.ndarray, origin, voxel_size: float, res
         return (st, None, None) if with_stats else (st, None)
     grid = out.reshape(res, res, W)
     if with_stats:
-        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2]),
+                      "rows_with_samples": int(stats[3])}
     return grid
 
 
@@ -229,14 +232,15 @@ def voxelize_grid_fixed(xyz: np.ndarray, tets: np.ndarray, res, z0: int = 0, z1:
     x = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
     t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
     out, shape, z1 = _grid_out(res, z0, z1)
-    stats = np.zeros(3, dtype=np.int64)
+    stats = np.zeros(4, dtype=np.int64)
     st = lib.voxtet_oracle_voxelize_grid_fixed(_ptr(x), len(x), _ptr(t), len(t), _ptr(_res3(res)), int(mode),
                                                int(n_threads), int(z0), int(z1), _ptr(out), _ptr(stats))
     if st != OK:
         raise OracleError(st)
     grid = out[: int(np.prod(shape))].reshape(shape)
     if with_stats:
-        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2]),
+                      "rows_with_samples": int(stats[3])}
     return grid
 
 
@@ -248,7 +252,7 @@ def voxelize_grid(verts: np.ndarray, tets: np.ndarray, origin, voxel_size: float
     t = np.ascontiguousarray(tets, dtype=np.int32).reshape(-1, 4)
     o = np.ascontiguousarray(np.asarray(origin, dtype=np.float32).reshape(3))
     out, shape, z1 = _grid_out(res, z0, z1)
-    stats = np.zeros(3, dtype=np.int64)
+    stats = np.zeros(4, dtype=np.int64)
     st = lib.voxtet_oracle_voxelize_grid(_ptr(v), len(v), _ptr(t), len(t), _ptr(o), float(voxel_size),
                                          _ptr(_res3(res)), int(mode), int(n_threads), int(z0), int(z1), _ptr(out),
                                          _ptr(stats))
@@ -256,7 +260,8 @@ def voxelize_grid(verts: np.ndarray, tets: np.ndarray, origin, voxel_size: float
         raise OracleError(st)
     grid = out[: int(np.prod(shape))].reshape(shape)
     if with_stats:
-        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2])}
+        return grid, {"degenerate": int(stats[0]), "tested": int(stats[1]), "set": int(stats[2]),
+                      "rows_with_samples": int(stats[3])}
     return grid
 
 

@@ -286,8 +286,8 @@ static int voxelize_core(const int32_t *xyz, int64_t n_verts, const int32_t *tet
     int64_t chunk = 1;
     while (chunk * 64 < depth) chunk *= 2; /* at most 64 z-chunks */
     const int64_t n_chunks = depth > 0 ? (depth + chunk - 1) / chunk : 0;
-    int64_t tested = 0;
-#pragma omp parallel num_threads(team_size(n_threads)) reduction(+ : tested)
+    int64_t tested = 0, rows_hit = 0;
+#pragma omp parallel num_threads(team_size(n_threads)) reduction(+ : tested, rows_hit)
     {
 #pragma omp single
         note_team();
@@ -303,13 +303,18 @@ static int voxelize_core(const int32_t *xyz, int64_t n_verts, const int32_t *tet
             const int64_t l0 = b->lo[2] > c0 ? b->lo[2] : c0;
             const int64_t l1 = b->hi[2] < c1 ? b->hi[2] : c1;
             for (int64_t l = l0; l <= l1; ++l)
-                for (int64_t j = b->lo[1]; j <= b->hi[1]; ++j)
+                for (int64_t j = b->lo[1]; j <= b->hi[1]; ++j) {
+                    int hit = 0;
                     for (int64_t i = b->lo[0]; i <= b->hi[0]; ++i) {
                         int64_t P[3] = {(2 * i + 1) * s, (2 * j + 1) * s, (2 * l + 1) * s};
                         tested += 1;
-                        if (theorem1_inside(V[0], V[1], V[2], V[3], P, mode == 1))
+                        if (theorem1_inside(V[0], V[1], V[2], V[3], P, mode == 1)) {
                             out_bits[((l - z0) * ry + j) * W + (i >> 5)] |= (uint32_t)1u << (i & 31);
+                            hit = 1;
+                        }
                     }
+                    rows_hit += hit;
+                }
         }
     }
     }
@@ -320,6 +325,7 @@ static int voxelize_core(const int32_t *xyz, int64_t n_verts, const int32_t *tet
         stats[0] = degenerate;
         stats[1] = tested;
         stats[2] = set;
+        stats[3] = rows_hit;
     }
     return OR_OK;
 }
@@ -328,7 +334,7 @@ static int voxelize_core(const int32_t *xyz, int64_t n_verts, const int32_t *tet
 int voxtet_oracle_voxelize_fixed_slab(const int32_t *xyz, int64_t n_verts, const int32_t *tets, int64_t n_tets,
                                       int32_t res, int32_t mode, int32_t n_threads, int32_t z0, int32_t z1,
                                       uint32_t *out_bits,
-                                      int64_t *stats /* [3]: degenerate tets, samples tested, bits set */) {
+                                      int64_t *stats /* [4]: degenerate tets, samples tested, bits set, (tet, x-row) pairs holding a sample */) {
     int k = log2_res(res);
     if (k < 0) return OR_ERR_RES;
     const int32_t r3[3] = {res, res, res};

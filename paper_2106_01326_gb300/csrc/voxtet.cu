@@ -2016,6 +2016,15 @@ extern "C" int voxelize_tets_noalloc(const float *d_verts, int64_t n_verts, cons
                        (size_t)VOXTET_NOALLOC_SCRATCH_BYTES, &o, stream);
 }
 
+// The status word sits at the start of the fixed array (its workspace header).
+extern "C" int voxtet_noalloc_status_async(int32_t *status_word, void *stream) {
+  if (!status_word) return VOXTET_ERR_ARG;
+  void *ws = nullptr;
+  const int st = noalloc_scratch(ws);
+  if (st != VOXTET_OK) return st;
+  return voxtet_status_async(ws, status_word, stream);
+}
+
 // ------------------------------------------------------------------ brick-sparse output
 //
 // Section 5 ("Octrees") notes that voxel data is usually stored sparsely.  Here a grid

@@ -27,6 +27,7 @@ EXPORTED = (
     "voxelize_tets_noalloc", "voxtet_batch_workspace_size", "voxelize_tets_batched", "voxtet_plan_create",
     "voxtet_plan_run", "voxtet_plan_query", "voxtet_plan_wait", "voxtet_plan_destroy",
     "voxtet_sparse_scratch_size", "voxelize_tets_sparse", "voxtet_status_async", "voxtet_status_of_word",
+    "voxtet_noalloc_status_async",
 )
 SPARSE_MAX_SIDE = 65536
 BRICK_WORDS = 64
@@ -106,6 +107,8 @@ def load(path: Optional[str] = None):
         lib.voxelize_tets_noalloc.argtypes = [P, i64, P, i64, ctypes.POINTER(f32 * 3), f32, i32, P,
                                               ctypes.POINTER(Opts), P]
         lib.voxelize_tets_noalloc.restype = ctypes.c_int
+        lib.voxtet_noalloc_status_async.argtypes = [P, P]
+        lib.voxtet_noalloc_status_async.restype = ctypes.c_int
         JP = ctypes.POINTER(Job)
         lib.voxtet_batch_workspace_size.argtypes = [JP, i32, i32]
         lib.voxtet_batch_workspace_size.restype = sz
@@ -357,9 +360,11 @@ def read_stats(workspace, stream=None) -> dict:
 def voxelize_noalloc(verts, tets, origin: Sequence[float], voxel_size: float, res: int, out, mode: int = 0,
                      use_filter: bool = True, sync: bool = True, stream=None) -> int:
     """Voxelize into ``out`` using the library's fixed device scratch instead of a
-    workspace, for callers that cannot allocate device memory when they call (see
-    voxelize_tets_noalloc in include/voxtet.h).  ``out`` must be preallocated;
-    returns the status code."""
+    workspace, for callers that cannot allocate device memory when they call (a host
+    application that owns the device-memory budget, a loop that must not enter the
+    allocator; see voxelize_tets_noalloc in include/voxtet.h).  ``out`` must be
+    preallocated; returns the status code (with ``sync`` False, the device-detected
+    part comes from ``noalloc_status_async``)."""
     torch = _torch()
     lib = load()
     _check_cuda_tensor(verts, "verts", torch.float32)
@@ -370,3 +375,17 @@ def voxelize_noalloc(verts, tets, origin: Sequence[float], voxel_size: float, re
     return int(lib.voxelize_tets_noalloc(verts.data_ptr(), verts.shape[0], tets.data_ptr(), tets.shape[0],
                                          ctypes.byref(org), float(voxel_size), int(res), out.data_ptr(),
                                          ctypes.byref(o), _stream_ptr(stream)))
+
+
+def noalloc_status_async(status_word, stream=None) -> int:
+    """Enqueue a copy of the last voxelize_noalloc call's status word into ``status_word``
+    (a one-element int32 tensor, pinned host or device) without synchronizing; read it with
+    ``status_of_word`` once the stream has passed.  Returns the enqueue status."""
+    torch = _torch()
+    if not isinstance(status_word, torch.Tensor) or status_word.dtype != torch.int32 or status_word.numel() < 1:
+        raise TypeError("status_word must be an int32 tensor with at least one element")
+    return int(load().voxtet_noalloc_status_async(status_word.data_ptr(), _stream_ptr(stream)))
+
+
+def status_of_word(word: int) -> int:
+    return int(load().voxtet_status_of_word(int(word)))

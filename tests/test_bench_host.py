@@ -27,3 +27,12 @@ def test_recorded_traffic_only_for_matching_sources(monkeypatch):
     assert bench.recorded_traffic("torus_48") is None  # another workload
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "0" * 64)
     assert bench.recorded_traffic("sliver_60") is None  # sources changed since the capture
+
+
+def test_alu_roofline_counts_rows_with_samples_when_known():
+    """With the oracle's count of rows holding a sample, the per-row work is counted on those
+    (the work no method avoids), not on the candidate rows the kernel visited."""
+    r = bench.alu_roofline(rows=1000, tets=10, kernel_ms=1.0, rows_with_samples=700)
+    assert r["algorithmic_ops"] == bench.ALU_OPS_PER_ROW * 700 + bench.ALU_OPS_PER_TET * 10
+    assert r["rows_candidate"] == 1000 and r["rows_with_samples"] == 700
+    assert r["frac"] < bench.alu_roofline(rows=1000, tets=10, kernel_ms=1.0)["frac"]

@@ -1,8 +1,9 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle, bit for bit.
 
-Small and medium cases are compared element by element over the whole grid;
-the full-size single-mesh workloads, in the launch configuration the benchmark
-times, are compared on sampled z-slabs the oracle computes directly.
+Small and medium cases are compared element by element over the whole grid, and
+so is the benchmark's workload (the 1.3M-tet sliver mesh at 512^3) in every
+launch shape the autotuner can pick; the 1024^3 and larger grids are compared
+on sampled z-slabs the oracle computes directly.
 """
 import numpy as np
 import pytest
@@ -291,6 +292,29 @@ def test_full_size_sliver_60_at_512(vt):
     assert stats["degenerate_tets"] > 0  # snapped slivers that became exactly flat
     assert stats["rows"] > 0
     assert stats["fallback_rows"] < 0.01 * stats["rows"]
+
+
+@pytest.fixture(scope="module")
+def sliver_512_oracle():
+    """The whole 512^3 grid of the benchmark mesh from the oracle (all host cores)."""
+    c = mg.single_mesh_config("sliver_60")
+    st, xyz = oracle.snap(c["verts"], c["origin"], c["voxel_size"], c["res"])
+    assert st == 0
+    return c, oracle.voxelize_fixed(xyz, c["tets"], c["res"])
+
+
+@pytest.mark.parametrize("span_rows,row_cull", [(0, 0), (1024, 1), (256, 1), (512, 2), (64, 1)])
+def test_full_grid_sliver_60_at_512(vt, sliver_512_oracle, span_rows, row_cull):
+    """The benchmark's workload compared with the oracle over every sample of the grid, in each
+    launch shape the autotuner can choose (span sizes, culling on and off)."""
+    import torch
+
+    c, ref = sliver_512_oracle
+    res = c["res"]
+    ws = vt.alloc_workspace(len(c["tets"]), len(c["verts"]), res)
+    g = vt.voxelize(_dev(c["verts"], torch.float32), _dev(c["tets"], torch.int32), c["origin"], c["voxel_size"], res,
+                    workspace=ws, span_rows=span_rows, row_cull=row_cull)
+    assert_same(g.cpu().numpy().view(np.uint32), ref, res, f"sliver_60 span_rows={span_rows} row_cull={row_cull}")
 
 
 def test_full_size_sliver_60_at_1024(vt):

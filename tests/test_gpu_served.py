@@ -2,11 +2,14 @@
 
 A small arena forces admission stalls, several plan slots keep batches in flight
 at once, and every finished request's grid is compared bit for bit with the same
-request voxelized alone.  The autotuner is exercised on the same meshes.
+request voxelized alone, and, in a stream of more than 200 requests that includes
+the pool's largest and smallest meshes, with the CPU oracle's grid.  The
+autotuner is exercised on the same meshes.
 """
 import numpy as np
 import pytest
 
+import oracle
 from paper_2106_01326_gb300 import meshgen as mg
 
 pytestmark = pytest.mark.gpu
@@ -68,6 +71,44 @@ def test_served_results_equal_alone(env, realtime):
         spans = [(t.launched_s, t.done_s, t.slot) for t in rep.tickets]
         overlap = any(a0 < b1 and b0 < a1 and sa != sb for a0, a1, sa in spans for b0, b1, sb in spans)
         assert overlap
+
+
+def test_served_results_equal_oracle(env):
+    """242 served requests (a Poisson stream plus the largest mesh at the finest grid and the
+    smallest at the coarsest), each grid compared bit for bit with the oracle's grid of the
+    same mesh and resolution; batches overlap and admissions stall on the arena."""
+    import torch
+
+    vt, batch, server, pool_dev = env
+    host = mg.mesh_pool(6, seed=91, tets_lo=500, tets_hi=60000)
+    sizes = [len(t) for _, t in host]
+    big, small = int(np.argmax(sizes)), int(np.argmin(sizes))
+    ress = (16, 32, 64, 128)
+    reqs = mg.poisson_stream(240, rate_per_s=1e6, n_pool=len(pool_dev), seed=17, resolutions=ress)
+    reqs.append(mg.Request(240, reqs[-1].arrival_s, big, max(ress)))
+    reqs.append(mg.Request(241, reqs[-1].arrival_s, small, min(ress)))
+    oracle.build()
+    ref = {}
+    for r in reqs:
+        key = (r.mesh_id, r.res)
+        if key not in ref:
+            v, t = host[key[0]]
+            ref[key] = torch.from_numpy(oracle.voxelize(v, t, (0, 0, 0), 1.0 / key[1], key[1]).view(np.int32)).cuda()
+    seen = {}
+
+    def check(tk, grid):
+        seen[tk.rid] = bool(torch.equal(grid, ref[(tk.mesh_id, tk.res)]))
+
+    srv = server.Server(pool_dev, arena_bytes=6 * server.grid_bytes(128), n_slots=3,
+                        slot_workspace_bytes=64 << 20, max_jobs=16, on_result=check)
+    try:
+        rep = srv.serve(reqs, realtime=False)
+    finally:
+        srv.close()
+    assert len(seen) == len(reqs) >= 200
+    assert all(seen.values()), sorted(rid for rid, ok in seen.items() if not ok)
+    assert all(t.status == vt.OK for t in rep.tickets)
+    assert rep.admission_stalls > 0 and rep.batches > 10
 
 
 def test_served_strict_mode_equals_alone(env):

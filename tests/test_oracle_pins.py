@@ -123,10 +123,16 @@ def test_kuhn_tet_counts_closed_form(oracle_lib, res, p, q):
     xyz, tets = _cube_tets(2 * s * p, 2 * s * q)
     total = 0
     for t in range(6):
-        occ = oracle.unpack(oracle.voxelize_fixed(xyz, tets[t:t + 1], res), res)
+        g, st = oracle.voxelize_fixed(xyz, tets[t:t + 1], res, with_stats=True)
+        occ = oracle.unpack(g, res)
         assert occ.sum() == math.comb(n + 2, 3)
+        # x-rows (j, l) holding a sample: the (y, z) order the tet fixes (j >= l or l >= j), with a
+        # sample i always available between them, so n(n+1)/2 whichever slot x takes in the order
+        assert st["rows_with_samples"] == n * (n + 1) // 2
         total += int(occ.sum())
     assert total == n * (n + 1) * (n + 2)
+    _, st = oracle.voxelize_fixed(xyz, tets, res, with_stats=True)
+    assert st["rows_with_samples"] == 3 * n * (n + 1)
 
 
 def test_plain_lattice_fills_grid(oracle_lib):

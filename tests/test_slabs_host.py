@@ -71,3 +71,38 @@ def test_slice_weights_count_covering_tets():
     # the boundary 0.95 of a float32 0.95 would fall just below the sample, so tet 1 ends at 0.97
     expect = np.array([0, 1, 1, 1, 2, 2, 1, 1, 1, 1], dtype=np.float64)
     assert np.array_equal(w, expect)
+
+
+@pytest.mark.parametrize("world", [2, 4])
+def test_slab_mesh_with_compacted_vertices_equals_slab_of_whole_mesh(world):
+    """slab_mesh renumbers a slab's tets onto only the vertices they name; the slab's bits do not
+    change (the snap is per vertex), and no unused vertex is kept."""
+    for name, v, t, origin, h, res3 in _meshes():
+        w = slabs.slice_weights(v, t, origin, h, res3[2])
+        for z0, z1 in slabs.slab_cuts(res3[2], world, w):
+            sv, st = slabs.slab_mesh(v, t, origin, h, z0, z1)
+            assert len(np.unique(st)) == len(sv) <= len(v)
+            whole = oracle.voxelize_grid(v, t, origin, h, res3, z0, z1)
+            part = oracle.voxelize_grid(sv, st, origin, h, res3, z0, z1)
+            assert np.array_equal(whole, part), (name, z0, z1)
+
+
+def test_slab_helpers_reject_what_the_whole_mesh_call_rejects():
+    """A negative or too-large index, or a non-finite coordinate, raises instead of being dropped
+    from (or wrapped into) a slab: the whole-mesh call reports such a mesh, so a slab must too."""
+    v = np.array([[0.1, 0.1, 0.1], [0.9, 0.1, 0.1], [0.1, 0.9, 0.1], [0.1, 0.1, 0.9]], dtype=np.float32)
+    good = np.array([[0, 1, 2, 3]], dtype=np.int32)
+    assert len(slabs.tets_for_slab(v, good, (0, 0, 0), 0.1, 0, 10)) == 1
+    for bad_t in (np.array([[0, 1, 2, -1]], dtype=np.int32), np.array([[0, 1, 2, 4]], dtype=np.int32)):
+        for fn in (slabs.tets_for_slab, slabs.slab_mesh):
+            with pytest.raises(ValueError):
+                fn(v, bad_t, (0, 0, 0), 0.1, 0, 10)
+        with pytest.raises(ValueError):
+            slabs.slice_weights(v, bad_t, (0, 0, 0), 0.1, 10)
+    for bad in (np.nan, np.inf):
+        vb = v.copy()
+        vb[3, 2] = bad
+        with pytest.raises(ValueError):
+            slabs.tets_for_slab(vb, good, (0, 0, 0), 0.1, 0, 10)
+        with pytest.raises(ValueError):
+            slabs.slab_mesh(vb, good, (0, 0, 0), 0.1, 0, 10)
