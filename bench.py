@@ -37,6 +37,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default="sliver_60")
     ap.add_argument("--span-rows", type=int, default=0)
+    ap.add_argument("--kernel", type=int, default=0, help="scanline work distribution: 0 auto, 1 spans, 2 slice units")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--slab", type=int, default=128, help="z-slices in the CPU oracle sample")
     ap.add_argument("--no-batched", action="store_true", help="skip the 256-mesh batched comparison")
@@ -612,6 +613,7 @@ def run_ours(args):
     # launch shape: the autotuner times span sizes and row culling on this mesh (untimed)
     from paper_2106_01326_gb300 import autotune
 
+    kernel = args.kernel
     if args.span_rows > 0:
         span_rows, row_cull, tuned = args.span_rows, 0, None
     else:
@@ -622,10 +624,10 @@ def run_ours(args):
         if slab:
             vt.voxelize_grid(v, t, cfg["origin"], cfg["voxel_size"], (res, res, res), z_range=z_range, out=grid,
                              workspace=ws, sync=False, span_rows=span_rows, row_cull=row_cull, profile=profile,
-                             stream=stream)
+                             stream=stream, kernel=kernel)
         else:
             vt.voxelize(v, t, cfg["origin"], cfg["voxel_size"], res, out=grid, workspace=ws, sync=False,
-                        span_rows=span_rows, row_cull=row_cull, profile=profile, stream=stream)
+                        span_rows=span_rows, row_cull=row_cull, profile=profile, stream=stream, kernel=kernel)
 
     def step():
         call(verts, tets, profile=True)

@@ -42,78 +42,10 @@
 
 #include "voxtet.h"
 #include "tet_math.cuh"
+#include "voxtet_device.cuh"
+#include "voxtet_slices.cuh"
 
 namespace voxtet {
-
-#ifndef VOXTET_MIN_BLOCKS
-#define VOXTET_MIN_BLOCKS 6  // resident blocks per SM the register budget is sized for
-#endif
-
-// Threads per block.  128-thread blocks of 512-tet tiles, 6 per SM, wait less at the tile
-// barriers than 256-thread blocks of 1024-tet tiles, 3 per SM (measured on GB300: sliver
-// mesh 512^3 kernel 336 -> 330 us, 1024^3 1117 -> 1088 us; torus 48^3 at 256^3 26.2 -> 24.1 us).
-constexpr int kBlock = 128;
-// Bounding-box rows per span (whole z-slices) when the caller does not choose (the
-// autotuner picks per mesh).  Measured on GB300 with the sliver and torus meshes: 256 is
-// best or within 13 % of it at every size except 1024^3, where 1024 (with 32-slice
-// spans) keeps a typical tet in one span, whose work estimate then sorts the lanes
-// evenly (sliver mesh 1.49 -> 1.15 ms); from 2048^3 spans that long can take twice as long.
-static __host__ __device__ int default_span_rows(int res) { return res >= 1024 && res < 2048 ? 1024 : 256; }
-constexpr int kCullMinRes = 256;        // automatic row culling from this resolution up
-constexpr int kMaxFilterRows = 8192;    // box rows per slice the fused kernel's slice table can hold
-// From this grid side up the filter clamps each face's bracket to the range where the
-// face can change a row (measured on GB300: 4% slower per row up to 1024^3 grids, where
-// few rows are uncertain; from 2048^3 it queues about 10x fewer rows and is faster)
-constexpr int kClampMinRes = 2048;
-
-// Workspace header (first 256 bytes of the workspace).
-struct Header {
-  int status_bits;
-  unsigned tetq_count;  // tets queued for the exact kernel
-  unsigned rowq_count;  // rows queued for the exact kernel (may exceed the capacity)
-  unsigned pad0;
-  unsigned long long tile_counter;
-  unsigned long long spans;
-  unsigned long long rows;
-  unsigned long long degenerate;
-  unsigned long long wide;
-  unsigned long long reserved[25];
-};
-static_assert(sizeof(Header) == 256, "header is 256 bytes");
-
-// A row the filter could not certify: tet index and (b, c) within its sample box.
-struct RowItem {
-  uint32_t tet;
-  uint16_t b, c;
-};
-
-struct Params {
-  const int4 *verts4;
-  const int4 *tets;
-  long long n_tets;
-  long long n_verts;
-  uint32_t *out;
-  Header *hdr;
-  uint32_t *tetq;   // [n_tets]
-  RowItem *rowq;    // [q_cap]
-  uint32_t *redo;   // [ceil(n_tets / 32)] bitmap
-  unsigned q_cap;
-  int rx, ry;       // samples per row and rows per slice
-  int z0, z1;       // slices z0 <= l < z1 are produced; out holds (z1 - z0) * ry * W words
-  int W;            // words per row, ceil(rx / 32)
-  int sh;           // log2 of the lattice step per voxel, 20 - ceil(log2(longest side))
-  int span_rows;    // target bounding-box rows per span
-  int exact_all;    // 1: every tet goes to the exact kernel
-  int max_slices;   // slices a span may hold (16 or 32): the slice table's rows in dynamic shared memory
-  int cull;         // 1: skip rows outside each slice's cross-section (batched kernel)
-  long long big_tiles;  // single-mesh launch: tiles of kTile tets before the kSmallTile tail
-  long long tile_stride;  // > 0: tile k holds tets k + j * tile_stride (slab launches), else contiguous tiles
-};
-
-// Row-queue capacity for a mesh of n_tets tets.
-static unsigned long long row_queue_capacity(long long n_tets) {
-  return (unsigned long long)(n_tets < 65536 ? 65536 : n_tets);
-}
 
 // ------------------------------------------------------------------ small kernels
 
@@ -196,58 +128,6 @@ __global__ void k_load_fixed(const int *__restrict__ xyz, long long n, int4 *__r
   if (err) atomicOr(&hdr->status_bits, err);
 }
 
-// ------------------------------------------------------------------ OR writes
-
-// OR the samples x0..x1 (inclusive, absolute x indices) into one row of words.
-// Used by the exact kernel; any word may be shared with other tets.
-__device__ __forceinline__ void or_span(uint32_t *__restrict__ row, int x0, int x1) {
-  const int w0 = x0 >> 5, w1 = x1 >> 5;
-  const uint32_t m0 = 0xFFFFFFFFu << (x0 & 31);
-  const uint32_t m1 = 0xFFFFFFFFu >> (31 - (x1 & 31));
-  if (w0 == w1) {
-    atomicOr(row + w0, m0 & m1);
-    return;
-  }
-  atomicOr(row + w0, m0);
-  for (int w = w0 + 1; w < w1; ++w) row[w] = 0xFFFFFFFFu;  // whole words: a plain store is an OR
-  atomicOr(row + w1, m1);
-}
-
-// The same for the hot loop, shaped to keep the lanes of a warp together: the first
-// word is always ORed (a zero mask when `live` is false), the second word only under
-// a predicate, and the rarely needed run of whole middle words behind a branch.
-__device__ __forceinline__ void or_span_lanes(uint32_t *__restrict__ row, int x0, int x1, bool live) {
-  const int w0 = x0 >> 5, w1 = x1 >> 5;
-  const uint32_t m1 = 0xFFFFFFFFu >> (31 - (x1 & 31));
-  uint32_t m0 = 0xFFFFFFFFu << (x0 & 31);
-  m0 = w0 == w1 ? (m0 & m1) : m0;
-  if (live) atomicOr(row + w0, m0);
-  if (live && w1 != w0) atomicOr(row + w1, m1);
-  if (live && w1 > w0 + 1) {
-    for (int w = w0 + 1; w < w1; ++w) row[w] = 0xFFFFFFFFu;
-  }
-}
-
-// ------------------------------------------------------------------ per-tet helpers
-
-// Loads tet t; false if an index is out of range (recorded) or a vertex failed its snap
-// (already recorded by the snap kernel).
-__device__ __forceinline__ bool load_tet(const Params &p, long long t, int3 V[4], int &err) {
-  const int4 q = p.tets[t];
-  const unsigned long long nv = (unsigned long long)p.n_verts;
-  if (q.x < 0 || q.y < 0 || q.z < 0 || q.w < 0 || (unsigned long long)q.x >= nv || (unsigned long long)q.y >= nv ||
-      (unsigned long long)q.z >= nv || (unsigned long long)q.w >= nv) {
-    err |= kErrIndex;
-    return false;
-  }
-  const int4 A = p.verts4[q.x], B = p.verts4[q.y], C = p.verts4[q.z], D = p.verts4[q.w];
-  V[0] = make_int3(A.x, A.y, A.z);
-  V[1] = make_int3(B.x, B.y, B.z);
-  V[2] = make_int3(C.x, C.y, C.z);
-  V[3] = make_int3(D.x, D.y, D.z);
-  return (A.w | B.w | C.w | D.w) == 0;
-}
-
 // Loads, orients (V6 > 0) and boxes a tet already known to be live; returns its extent.
 __device__ __forceinline__ int oriented_tet(const Params &p, long long t, int3 V[4], Box &bx) {
   int dummy = 0;
@@ -309,156 +189,6 @@ __device__ __forceinline__ uint32_t classify_tet(const Params &p, long long t, i
   }
   meta = (uint32_t)(sg < 0) | ((uint32_t)S << 1);
   return (uint32_t)((bx.nc + S - 1) / S);
-}
-
-// Edge lines of a tet for the per-slice row range, with the vertices sorted by z
-// (z0 <= z1 <= z2 <= z3).  Edge (p, q) crosses the plane at height Z at
-// y = y_p + (Z - z_p) k with k = (y_q - y_p) / (z_q - z_p) (k = 0 for horizontal edges,
-// whose end points the other edges also reach).  Z - z_p is exact in float
-// (|Z|, |z_p| <= 2^21) and k carries one rounding, so each crossing point is within
-// u 2^22 + u 2^21 < 0.4 lattice units of the true one.  Edge order: 01 02 03 12 13 23.
-struct EdgeLines {
-  float zp[6], yp[6], k[6];
-  int z1, z2;
-};
-
-__device__ __forceinline__ void edge_lines(const int3 V[4], EdgeLines &E) {
-  int z[4] = {V[0].z, V[1].z, V[2].z, V[3].z};
-  int y[4] = {V[0].y, V[1].y, V[2].y, V[3].y};
-#define VOXTET_CSWAP(a, b)                                  \
-  if (z[b] < z[a]) {                                        \
-    const int tz = z[a], ty = y[a];                         \
-    z[a] = z[b]; y[a] = y[b]; z[b] = tz; y[b] = ty;         \
-  }
-  VOXTET_CSWAP(0, 1)
-  VOXTET_CSWAP(2, 3)
-  VOXTET_CSWAP(0, 2)
-  VOXTET_CSWAP(1, 3)
-  VOXTET_CSWAP(1, 2)
-#undef VOXTET_CSWAP
-#pragma unroll
-  for (int e = 0; e < 6; ++e) {
-    const int pi = e < 3 ? 0 : (e < 5 ? 1 : 2);
-    const int qi = e < 3 ? e + 1 : (e < 5 ? e - 1 : 3);
-    const int dz = z[qi] - z[pi];
-    E.zp[e] = (float)z[pi];
-    E.yp[e] = (float)y[pi];
-    E.k[e] = dz != 0 ? __fdiv_rn((float)(y[qi] - y[pi]), (float)dz) : 0.f;
-  }
-  E.z1 = z[1];
-  E.z2 = z[2];
-}
-
-// Candidate rows [b_lo, b_hi] of the slice at height Z (inside the tet's z-range):
-// the cross-section's y-extent, widened by 2 lattice units, in row indices.
-__device__ __forceinline__ void slice_rows_sorted(const EdgeLines &E, int Z, int s, int sh, int j0, int nb,
-                                                  int &b_lo, int &b_hi) {
-  const float Zf = (float)Z;
-  const bool le1 = Z <= E.z1, le2 = Z <= E.z2, ge1 = Z >= E.z1, ge2 = Z >= E.z2;
-  const bool valid[6] = {le1, le2, true, ge1 && le2, ge1, ge2};
-  float ymin = 3.0e38f, ymax = -3.0e38f;
-#pragma unroll
-  for (int e = 0; e < 6; ++e) {
-    const float y = __fmaf_rn(Zf - E.zp[e], E.k[e], E.yp[e]);
-    if (valid[e]) {
-      ymin = fminf(ymin, y);
-      ymax = fmaxf(ymax, y);
-    }
-  }
-  const int ylo = (int)floorf(ymin) - 2, yhi = (int)ceilf(ymax) + 2;
-  b_lo = max(((ylo + s - 1) >> sh) - j0, 0);
-  b_hi = min(((yhi - s) >> sh) - j0, nb - 1);
-}
-
-// Queue row (b, c) of tet t for the exact kernel; if the row queue is full, flag the
-// whole tet for an exact redo instead.
-__device__ __forceinline__ void queue_row(const Params &p, long long t, int b, int c) {
-  const unsigned k = atomicAdd(&p.hdr->rowq_count, 1u);
-  if (k < p.q_cap) {
-    RowItem it;
-    it.tet = (uint32_t)t;
-    it.b = (uint16_t)b;
-    it.c = (uint16_t)c;
-    p.rowq[k] = it;
-  } else {
-    atomicOr(&p.redo[t >> 5], 1u << (t & 31));
-  }
-}
-
-// Rows allowed by a constraint that does not depend on x (a face parallel to the x
-// axis): lam = H0 + Dy b along the slice, exact.  Narrows [b_lo, b_hi] by bisection
-// on the monotone lam(b), probing only rows inside the box.
-template <bool STRICT>
-__device__ __forceinline__ void narrow_by_row_constraint(i64 H0, i64 Dy, int &b_lo, int &b_hi) {
-  if (b_lo > b_hi) return;
-  if (Dy == 0) {
-    if (!lam_ok<STRICT, i64>(H0)) b_hi = b_lo - 1;
-    return;
-  }
-  if (Dy > 0) {  // increasing: smallest b in [b_lo, b_hi + 1] that is ok
-    int x = b_lo, y = b_hi + 1;
-    while (x < y) {
-      const int mid = (x + y) >> 1;
-      if (lam_ok<STRICT, i64>(H0 + Dy * (i64)mid)) y = mid;
-      else x = mid + 1;
-    }
-    b_lo = x;
-  } else {  // decreasing: largest b in [b_lo - 1, b_hi] that is ok
-    int x = b_lo - 1, y = b_hi;
-    while (x < y) {
-      const int mid = (x + y + 1) >> 1;
-      if (lam_ok<STRICT, i64>(H0 + Dy * (i64)mid)) x = mid;
-      else y = mid - 1;
-    }
-    b_hi = x;
-  }
-}
-
-// Uncertain rows are first collected in a per-block shared-memory buffer and moved
-// to the global row queue with one atomic per tile, so that thousands of threads do
-// not contend on the queue counter.
-constexpr int kStage = 512;
-struct RowStage {
-  RowItem items[kStage];
-  uint32_t n;
-  uint32_t base;
-};
-
-__device__ __forceinline__ void queue_row_staged(const Params &p, RowStage &st, long long t, int b, int c) {
-  const uint32_t k = atomicAdd(&st.n, 1u);
-  if (k < (uint32_t)kStage) {
-    RowItem it;
-    it.tet = (uint32_t)t;
-    it.b = (uint16_t)b;
-    it.c = (uint16_t)c;
-    st.items[k] = it;
-  } else {
-    queue_row(p, t, b, c);
-  }
-}
-
-// Moves a block's staged rows to the global queue (all threads of the block call it).
-__device__ __forceinline__ void flush_stage(const Params &p, RowStage &st) {
-  __syncthreads();
-  const uint32_t n = min(st.n, (uint32_t)kStage);
-  if (n) {
-    if (threadIdx.x == 0) st.base = atomicAdd(&p.hdr->rowq_count, n);
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-      const unsigned k = st.base + i;
-      const RowItem it = st.items[i];
-      if (k < p.q_cap) p.rowq[k] = it;
-      else atomicOr(&p.redo[it.tet >> 5], 1u << (it.tet & 31));
-    }
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) st.n = 0;
-}
-
-// Exact conversion of an integral float in [0, 2^22) to int without the conversion
-// unit: adding 2^23 puts the integer in the low mantissa bits.
-__device__ __forceinline__ int small_float_to_int(float f) {
-  return __float_as_int(__fadd_rn(f, 8388608.0f)) - 0x4B000000;
 }
 
 // Slices per span: the slice table (one column per thread, in dynamic shared memory)
@@ -674,20 +404,22 @@ struct TileSmem {
   RowStage stage;
 };
 
-struct TileCounters {
-  int err = 0;
-  unsigned degenerate = 0, wide = 0, rows = 0;
-  unsigned long long spans = 0;
-};
-
 // Phases (1)-(4) for tets [base, base + kTile) of one mesh.  All threads of the block
 // call it; it begins and ends with the block in step.
 // Tet in slot i of the tile that starts at `base`: base + i, or, in a slab launch
 // (STRIDED, base = the tile's number), base + i * tile_stride, so that the tets of the
 // slab -- one contiguous run in a mesh numbered along z -- spread over every tile.
+// In list mode (the tets the slice-unit kernel left over), slot i of the tile starting at
+// list position `base` holds tetq[n_tets - 1 - (base + i)].  Returns -1 past `end`.
 template <bool STRIDED>
-__device__ __forceinline__ long long tile_tet(const Params &p, long long base, long long i) {
-  return STRIDED ? base + i * p.tile_stride : base + i;
+__device__ __forceinline__ long long tile_tet(const Params &p, long long base, long long i, long long end) {
+  if (STRIDED) {
+    const long long t = base + i * p.tile_stride;
+    return t < end ? t : -1;
+  }
+  const long long k = base + i;
+  if (k >= end) return -1;
+  return p.list_mode ? (long long)p.tetq[p.n_tets - 1 - k] : k;
 }
 
 // Slots whose tet is at or past `end` are empty.
@@ -702,10 +434,10 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
   float wlo = 3.0e38f, whi = 0.f;
 #pragma unroll
   for (int k = 0; k < kPerThread; ++k) {
-    const long long t = tile_tet<STRIDED>(p, base, (long long)tid * kPerThread + k);
+    const long long t = tile_tet<STRIDED>(p, base, (long long)tid * kPerThread + k, end);
     work[k] = 0.f;
     uint32_t mt = 0;
-    cnt[k] = t < end ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide, work[k], mt) : 0u;
+    cnt[k] = t >= 0 ? classify_tet(p, t, ctr.err, ctr.degenerate, ctr.wide, work[k], mt) : 0u;
     sm.meta[tid * kPerThread + k] = (uint8_t)mt;
     if (cnt[k]) {
       work[k] /= (float)cnt[k];  // per span
@@ -819,7 +551,7 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
       }
       q = i - sm.off[a];
     }
-    const long long t = tile_tet<STRIDED>(p, base, a);
+    const long long t = tile_tet<STRIDED>(p, base, a, end);
     int3 V[4];
     Box bx;
     int dummy = 0;
@@ -831,27 +563,6 @@ __device__ __forceinline__ void process_tile(const Params &p, long long base, lo
     ctr.rows += run_span<STRICT, CULL, CLAMP>(p, t, V, bx, c0, min(c0 + S, bx.nc), slice_tab, sm.stage, (mt & 1u) != 0);
   }
   flush_stage(p, sm.stage);
-}
-
-// Adds a block's counters to a mesh's header: one atomic per warp and counter.
-__device__ __forceinline__ void flush_counters(Header *hdr, TileCounters &ctr) {
-  const int lane = threadIdx.x & 31;
-  unsigned long long rows_w = ctr.rows, deg_w = ctr.degenerate, wide_w = ctr.wide;
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    rows_w += __shfl_down_sync(0xFFFFFFFFu, rows_w, d);
-    deg_w += __shfl_down_sync(0xFFFFFFFFu, deg_w, d);
-    wide_w += __shfl_down_sync(0xFFFFFFFFu, wide_w, d);
-  }
-  const int err = __reduce_or_sync(0xFFFFFFFFu, ctr.err);
-  if (lane == 0) {
-    if (rows_w) atomicAdd(&hdr->rows, rows_w);
-    if (deg_w) atomicAdd(&hdr->degenerate, deg_w);
-    if (wide_w) atomicAdd(&hdr->wide, wide_w);
-    if (err) atomicOr(&hdr->status_bits, err);
-  }
-  if (threadIdx.x == 0 && ctr.spans) atomicAdd(&hdr->spans, ctr.spans);
-  ctr = TileCounters();
 }
 
 // The slice table lives in dynamic shared memory: p.max_slices rows of kBlock words.
@@ -868,10 +579,12 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
   TileCounters ctr;
   if (threadIdx.x == 0) sm.stage.n = 0;
   // Guided tiles: full tiles first, then quarter tiles for the last stretch (about two
-  // per block), so that blocks finish close together at the end of the kernel.
+  // per block), so that blocks finish close together at the end of the kernel.  In list
+  // mode the tets are the ones the slice-unit kernel listed (stream-ordered before this launch).
   const long long big = p.big_tiles;
+  const long long n_tets = p.list_mode ? min((long long)p.hdr->listq_count, p.n_tets) : p.n_tets;
   for (;;) {
-    if (threadIdx.x == 0) tile_s = atomicAdd(&p.hdr->tile_counter, 1ull);
+    if (threadIdx.x == 0) tile_s = atomicAdd(p.list_mode ? &p.hdr->list_tile_counter : &p.hdr->tile_counter, 1ull);
     __syncthreads();
     const long long tile = (long long)tile_s;
     if (STRIDED) {
@@ -880,8 +593,8 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
       continue;
     }
     const long long base = tile < big ? tile * kTile : big * kTile + (tile - big) * kSmallTile;
-    if (base >= p.n_tets) break;
-    const long long end = min(p.n_tets, base + (tile < big ? kTile : kSmallTile));
+    if (base >= n_tets) break;
+    const long long end = min(n_tets, base + (tile < big ? kTile : kSmallTile));
     process_tile<STRICT, CULL, CLAMP, false>(p, base, end, sm, slice_tab, ctr);
   }
   flush_counters(p.hdr, ctr);
@@ -1322,7 +1035,16 @@ static int check_opts(const voxtet_opts &o) {
   if (o.block != 0 && o.block != kBlock) return VOXTET_ERR_ARG;
   if (o.profile != 0 && o.profile != 1) return VOXTET_ERR_ARG;
   if (o.row_cull < 0 || o.row_cull > 2) return VOXTET_ERR_ARG;
+  if (o.kernel < 0 || o.kernel > 2) return VOXTET_ERR_ARG;
   return VOXTET_OK;
+}
+
+// Which distribution of the scanline work a call uses (both give the same grid).
+static bool use_slice_units(const voxtet_opts &o, const GridDims &g) {
+  if (o.kernel == 2) return true;
+  if (o.kernel == 1) return false;
+  (void)g;
+  return false;
 }
 
 // Shared tail of both entry points: vertices are already in the workspace.
@@ -1331,7 +1053,7 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   if (n_tets > 0) {
-    Params p;
+    Params p{};  // every field zero unless set below (list_mode = 0)
     p.verts4 = w.verts4;
     p.tets = reinterpret_cast<const int4 *>(tets);
     p.n_tets = n_tets;
@@ -1378,7 +1100,20 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     }
     if (grid > tiles) grid = tiles;
     if (o.profile && profile_begin(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
-    voxelize_kernel(variant)<<<(unsigned)grid, kBlock, slice_table_bytes(p.max_slices), stream>>>(p);
+    if (use_slice_units(o, g)) {
+      // slice units for the tets that fit them, then the span kernel over the tets it listed
+      if (launch_slices(p, variant, dev->sms, stream) != VOXTET_OK) return VOXTET_ERR_CUDA;
+      g_launches.fetch_add(1);
+      Params q = p;
+      q.list_mode = 1;
+      q.tile_stride = 0;
+      q.big_tiles = (n_tets + kTile - 1) / kTile + 1;  // whole tiles only
+      const int lv = variant & 7;
+      const long long lgrid = (long long)dev->sms * (dev->occ[lv] > 0 ? dev->occ[lv] : 1);
+      voxelize_kernel(lv)<<<(unsigned)lgrid, kBlock, slice_table_bytes(q.max_slices), stream>>>(q);
+    } else {
+      voxelize_kernel(variant)<<<(unsigned)grid, kBlock, slice_table_bytes(p.max_slices), stream>>>(p);
+    }
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
     if (o.profile) {
@@ -1489,6 +1224,7 @@ void voxtet_default_opts(voxtet_opts *o) {
   o->block = 0;
   o->profile = 0;
   o->row_cull = 0;
+  o->kernel = 0;
 }
 
 size_t voxtet_workspace_size(int64_t n_tets, int64_t n_verts, int32_t res) {

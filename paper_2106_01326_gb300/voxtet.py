@@ -37,7 +37,7 @@ NOALLOC_SCRATCH_BYTES = 16 << 20
 class Opts(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("accumulate", ctypes.c_int32), ("use_filter", ctypes.c_int32),
                 ("sync", ctypes.c_int32), ("span_rows", ctypes.c_int32), ("block", ctypes.c_int32),
-                ("profile", ctypes.c_int32), ("row_cull", ctypes.c_int32)]
+                ("profile", ctypes.c_int32), ("row_cull", ctypes.c_int32), ("kernel", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -147,12 +147,17 @@ def workspace_size(n_tets: int, n_verts: int, res: int) -> int:
     return int(load().voxtet_workspace_size(int(n_tets), int(n_verts), int(res)))
 
 
+KERNEL_AUTO, KERNEL_SPANS, KERNEL_SLICES = 0, 1, 2
+
+
 def make_opts(mode: int = 0, accumulate: bool = False, use_filter: bool = True, sync: bool = True,
-              span_rows: int = 0, block: int = 0, profile: bool = False, row_cull: int = 0) -> Opts:
+              span_rows: int = 0, block: int = 0, profile: bool = False, row_cull: int = 0,
+              kernel: int = 0) -> Opts:
     o = Opts()
     load().voxtet_default_opts(ctypes.byref(o))
     o.mode, o.accumulate, o.use_filter, o.sync = int(mode), int(bool(accumulate)), int(bool(use_filter)), int(bool(sync))
     o.span_rows, o.block, o.profile, o.row_cull = int(span_rows), int(block), int(bool(profile)), int(row_cull)
+    o.kernel = int(kernel)
     return o
 
 
@@ -193,7 +198,7 @@ def alloc_workspace(n_tets: int, n_verts: int, res: int, device=None):
 def voxelize(verts, tets, origin: Sequence[float], voxel_size: float, res: int, out=None, workspace=None,
              mode: int = 0, accumulate: bool = False, use_filter: bool = True, sync: bool = True,
              span_rows: int = 0, stream=None, raise_on_error: bool = True, profile: bool = False,
-             row_cull: int = 0):
+             row_cull: int = 0, kernel: int = 0):
     """Grid (int32 tensor [res, res, W] of uint32 bit words) of a world-space mesh.
 
     verts: float32 CUDA [n_verts, 3]; tets: int32 CUDA [n_tets, 4].  Returns ``out``
@@ -209,7 +214,7 @@ def voxelize(verts, tets, origin: Sequence[float], voxel_size: float, res: int, 
     _check_cuda_tensor(out, "out", torch.int32)
     if workspace is None:
         workspace = alloc_workspace(n_t, n_v, res, verts.device)
-    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull)
+    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull, kernel=kernel)
     org = (ctypes.c_float * 3)(*[float(x) for x in origin])
     st = lib.voxelize_tets(verts.data_ptr(), n_v, tets.data_ptr(), n_t, ctypes.byref(org), float(voxel_size),
                            int(res), out.data_ptr(), workspace.data_ptr(), workspace.numel(), ctypes.byref(o),
@@ -223,7 +228,7 @@ def voxelize(verts, tets, origin: Sequence[float], voxel_size: float, res: int, 
 
 def voxelize_fixed(xyz, tets, res: int, out=None, workspace=None, mode: int = 0, accumulate: bool = False,
                    use_filter: bool = True, sync: bool = True, span_rows: int = 0, stream=None,
-                   raise_on_error: bool = True, profile: bool = False, row_cull: int = 0):
+                   raise_on_error: bool = True, profile: bool = False, row_cull: int = 0, kernel: int = 0):
     """Grid of a mesh whose vertices are already on the 2^20-per-grid lattice (int32 [n, 3])."""
     torch = _torch()
     lib = load()
@@ -235,7 +240,7 @@ def voxelize_fixed(xyz, tets, res: int, out=None, workspace=None, mode: int = 0,
     _check_cuda_tensor(out, "out", torch.int32)
     if workspace is None:
         workspace = alloc_workspace(n_t, n_v, res, xyz.device)
-    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull)
+    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull, kernel=kernel)
     st = lib.voxelize_tets_fixed(xyz.data_ptr(), n_v, tets.data_ptr(), n_t, int(res), out.data_ptr(),
                                  workspace.data_ptr(), workspace.numel(), ctypes.byref(o), _stream_ptr(stream))
     if raise_on_error:
@@ -256,7 +261,8 @@ def alloc_grid_dims(res3: Sequence[int], z_range: Optional[Tuple[int, int]] = No
 def voxelize_grid(verts, tets, origin: Sequence[float], voxel_size: float, res3: Sequence[int],
                   z_range: Optional[Tuple[int, int]] = None, out=None, workspace=None, mode: int = 0,
                   accumulate: bool = False, use_filter: bool = True, sync: bool = True, span_rows: int = 0,
-                  stream=None, raise_on_error: bool = True, profile: bool = False, row_cull: int = 0):
+                  stream=None, raise_on_error: bool = True, profile: bool = False, row_cull: int = 0,
+                  kernel: int = 0):
     """General grid res3 = (rx, ry, rz), any sides in [1, MAX_RES], or its z-slab
     ``z_range`` = (z_begin, z_end): int32 tensor [z_end - z_begin, ry, ceil(rx / 32)]."""
     torch = _torch()
@@ -271,7 +277,7 @@ def voxelize_grid(verts, tets, origin: Sequence[float], voxel_size: float, res3:
     _check_cuda_tensor(out, "out", torch.int32)
     if workspace is None:
         workspace = alloc_workspace(n_t, n_v, max(int(x) for x in res3), verts.device)
-    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull)
+    o = make_opts(mode, accumulate, use_filter, sync, span_rows, profile=profile, row_cull=row_cull, kernel=kernel)
     org = (ctypes.c_float * 3)(*[float(x) for x in origin])
     r3 = (ctypes.c_int32 * 3)(rx, ry, rz)
     st = lib.voxelize_tets_grid(verts.data_ptr(), n_v, tets.data_ptr(), n_t, ctypes.byref(org), float(voxel_size),
@@ -305,7 +311,8 @@ def default_slab_depth(res3: Sequence[int], budget_bytes: int = 128 << 20) -> in
 
 def voxelize_sparse(verts, tets, origin: Sequence[float], voxel_size: float, res3: Sequence[int],
                     slab_depth: int = 0, max_bricks: Optional[int] = None, workspace=None, scratch=None,
-                    mode: int = 0, use_filter: bool = True, span_rows: int = 0, row_cull: int = 0, stream=None):
+                    mode: int = 0, use_filter: bool = True, span_rows: int = 0, row_cull: int = 0, stream=None,
+                    kernel: int = 0):
     """Brick-sparse grid: (keys int64 [n], words int32 [n, 64]) of the non-empty 32 x 8 x 8 bricks,
     keys bx | by << 16 | bz << 32 in increasing order.  Grows the output and retries once if
     ``max_bricks`` is too small."""
@@ -324,7 +331,7 @@ def voxelize_sparse(verts, tets, origin: Sequence[float], voxel_size: float, res
     if max_bricks is None:
         rx, ry, rz = (int(x) for x in res3)
         max_bricks = min(((rx + 31) // 32) * ((ry + 7) // 8) * ((rz + 7) // 8), 1 << 20)
-    o = make_opts(mode, False, use_filter, True, span_rows, row_cull=row_cull)
+    o = make_opts(mode, False, use_filter, True, span_rows, row_cull=row_cull, kernel=kernel)
     org = (ctypes.c_float * 3)(*[float(x) for x in origin])
     for attempt in range(2):
         keys = torch.empty(max(int(max_bricks), 1), dtype=torch.int64, device=dev)

@@ -19,3 +19,28 @@ def oracle_lib():
 
     oracle.build()
     return oracle
+
+
+class KernelBound:
+    """The voxtet binding with the work distribution of the scanline step fixed: calls of the
+    voxelize functions get ``kernel=K`` unless they pass one (1 = spans, 2 = slice units).
+    GPU parity tests run once per distribution, since both must give the oracle's grid."""
+
+    _BOUND = ("voxelize", "voxelize_fixed", "voxelize_grid", "voxelize_sparse")
+
+    def __init__(self, module, kernel: int):
+        self._m = module
+        self.kernel = int(kernel)
+
+    def __getattr__(self, name):
+        a = getattr(self._m, name)
+        if name in self._BOUND:
+            def call(*args, **kw):
+                kw.setdefault("kernel", self.kernel)
+                return a(*args, **kw)
+            return call
+        return a
+
+
+KERNELS = [1, 2]
+KERNEL_IDS = ["spans", "slices"]

@@ -45,7 +45,8 @@ def test_exports_every_declared_symbol(lib):
 def test_host_side_calls(lib):
     o = vt.Opts()
     lib.voxtet_default_opts(ctypes.byref(o))
-    assert (o.mode, o.accumulate, o.use_filter, o.sync, o.span_rows, o.block, o.profile, o.row_cull) == (0, 0, 1, 1, 0, 0, 0, 0)
+    assert (o.mode, o.accumulate, o.use_filter, o.sync, o.span_rows, o.block, o.profile, o.row_cull,
+            o.kernel) == (0, 0, 1, 1, 0, 0, 0, 0, 0)
     assert vt.workspace_size(10, 100, 64) >= 256 + 16 * 100
     assert vt.workspace_size(-1, 1, 64) == 0
     assert vt.strerror(vt.ERR_INDEX) == "tetrahedron vertex index out of range"

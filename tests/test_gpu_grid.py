@@ -6,6 +6,7 @@ grid they partition.
 """
 import numpy as np
 import pytest
+from conftest import KERNEL_IDS, KERNELS, KernelBound
 
 import oracle
 from paper_2106_01326_gb300 import meshgen as mg
@@ -13,8 +14,8 @@ from paper_2106_01326_gb300 import meshgen as mg
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def vt():
+@pytest.fixture(scope="module", params=KERNELS, ids=KERNEL_IDS)
+def vt(request):
     import torch
 
     if not torch.cuda.is_available():
@@ -24,7 +25,7 @@ def vt():
 
     vbuild.build()
     voxtet.load()
-    return voxtet
+    return KernelBound(voxtet, request.param)
 
 
 def _mesh_for(res3, N=6, jitter=0.3, seed=0, overhang=1.08):

@@ -7,6 +7,7 @@ on sampled z-slabs the oracle computes directly.
 """
 import numpy as np
 import pytest
+from conftest import KERNEL_IDS, KERNELS, KernelBound
 
 import oracle
 from paper_2106_01326_gb300 import meshgen as mg
@@ -16,8 +17,8 @@ pytestmark = pytest.mark.gpu
 L = 1 << 20
 
 
-@pytest.fixture(scope="module")
-def vt():
+@pytest.fixture(scope="module", params=KERNELS, ids=KERNEL_IDS)
+def vt(request):
     import torch
 
     if not torch.cuda.is_available():
@@ -28,7 +29,7 @@ def vt():
     vbuild.build()
     oracle.build()
     voxtet.load()
-    return voxtet
+    return KernelBound(voxtet, request.param)
 
 
 def _dev(a, dtype):

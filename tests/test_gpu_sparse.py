@@ -11,6 +11,7 @@ import ctypes
 
 import numpy as np
 import pytest
+from conftest import KERNEL_IDS, KERNELS, KernelBound
 
 import oracle
 from paper_2106_01326_gb300 import meshgen as mg
@@ -18,8 +19,8 @@ from paper_2106_01326_gb300 import meshgen as mg
 pytestmark = pytest.mark.gpu
 
 
-@pytest.fixture(scope="module")
-def vt():
+@pytest.fixture(scope="module", params=KERNELS, ids=KERNEL_IDS)
+def vt(request):
     import torch
 
     if not torch.cuda.is_available():
@@ -29,7 +30,7 @@ def vt():
 
     vbuild.build()
     voxtet.load()
-    return voxtet
+    return KernelBound(voxtet, request.param)
 
 
 def _mesh(res3, fill=(1.0, 1.0, 1.0), N=6, seed=0):
