@@ -39,13 +39,13 @@ class HostPipeline:
     first job whose device-detected status is not OK."""
 
     def __init__(self, max_verts: int, max_tets: int, res: int, depth: int = 3, device=None, mode: int = 0,
-                 span_rows: int = 0, row_cull: int = 0):
+                 span_rows: int = 0, row_cull: int = 0, kernel: int = 0):
         import torch
 
         self._torch = torch
         dev = torch.device(device or "cuda")
         self.res = int(res)
-        self.kw = dict(mode=mode, span_rows=span_rows, row_cull=row_cull)
+        self.kw = dict(mode=mode, span_rows=span_rows, row_cull=row_cull, kernel=kernel)
         self.slots = [_Slot(torch, max_verts, max_tets, self.res, dev) for _ in range(max(1, int(depth)))]
         self.h2d = torch.cuda.Stream(device=dev)
         self.compute = torch.cuda.Stream(device=dev)

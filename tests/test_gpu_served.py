@@ -143,8 +143,10 @@ def test_autotune_keeps_grid_and_caches(env, tmp_path, monkeypatch):
     m = pool[int(np.argmax([p.n_tets for p in pool]))]
     res = 128
     r = autotune.tune(m.verts, m.tets, (0, 0, 0), 1.0 / res, res, spans=(64, 256), culls=(1, 2), reps=2)
-    assert r["span_rows"] in (64, 256) and r["row_cull"] in (1, 2)
+    assert r["kernel"] in (1, 2) and r["span_rows"] in (0, 64, 256) and r["row_cull"] in (1, 2)
+    assert len(r["table"]) == 6  # 2 span sizes x 2 culls, and slice units x 2 culls
     assert autotune.lookup(res)["span_rows"] == r["span_rows"]
-    assert autotune.settings_for(res) == (r["span_rows"], r["row_cull"])
-    g = vt.voxelize(m.verts, m.tets, (0, 0, 0), 1.0 / res, res, span_rows=r["span_rows"], row_cull=r["row_cull"])
+    assert autotune.settings_for(res) == (r["span_rows"], r["row_cull"], r["kernel"])
+    g = vt.voxelize(m.verts, m.tets, (0, 0, 0), 1.0 / res, res, span_rows=r["span_rows"], row_cull=r["row_cull"],
+                    kernel=r["kernel"])
     assert torch.equal(g, vt.voxelize(m.verts, m.tets, (0, 0, 0), 1.0 / res, res))
