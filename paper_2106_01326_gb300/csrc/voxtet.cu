@@ -583,6 +583,7 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p
   // mode the tets are the ones the slice-unit kernel listed (stream-ordered before this launch).
   const long long big = p.big_tiles;
   const long long n_tets = p.list_mode ? min((long long)p.hdr->listq_count, p.n_tets) : p.n_tets;
+  if (n_tets == 0) return;  // list mode with nothing listed (the block is still in step: no barrier yet)
   for (;;) {
     if (threadIdx.x == 0) tile_s = atomicAdd(p.list_mode ? &p.hdr->list_tile_counter : &p.hdr->tile_counter, 1ull);
     __syncthreads();
@@ -1109,9 +1110,10 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
       q.list_mode = 1;
       q.tile_stride = 0;
       q.big_tiles = (n_tets + kTile - 1) / kTile + 1;  // whole tiles only
+      // one block per SM: the list is usually empty or short (tets spanning more than 32
+      // slices or 1024 rows per slice), and an empty list then costs one short wave
       const int lv = variant & 7;
-      const long long lgrid = (long long)dev->sms * (dev->occ[lv] > 0 ? dev->occ[lv] : 1);
-      voxelize_kernel(lv)<<<(unsigned)lgrid, kBlock, slice_table_bytes(q.max_slices), stream>>>(q);
+      voxelize_kernel(lv)<<<(unsigned)dev->sms, kBlock, slice_table_bytes(q.max_slices), stream>>>(q);
     } else {
       voxelize_kernel(variant)<<<(unsigned)grid, kBlock, slice_table_bytes(p.max_slices), stream>>>(p);
     }
