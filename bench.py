@@ -85,11 +85,11 @@ def kernel_source_digest() -> str:
     return h.hexdigest()
 
 
-def recorded_traffic(workload: str):
-    """DRAM bytes per k_voxelize launch from profiles/k_voxelize_traffic.txt (one ncu
+def recorded_traffic(workload: str, kernel: str = "k_voxelize"):
+    """DRAM bytes per launch of the main kernel from profiles/<kernel>_traffic.txt (one ncu
     capture of this benchmark's command), or None if it was taken on other sources or
     another workload."""
-    p = os.path.join(ROOT, "profiles", "k_voxelize_traffic.txt")
+    p = os.path.join(ROOT, "profiles", f"{kernel}_traffic.txt")
     try:
         kv = {}
         with open(p) as f:
@@ -346,6 +346,16 @@ def batched_section(args, flush, stream):
     torch.cuda.synchronize()
     exact = all(bool(torch.equal(sp.out, r)) for sp, r in zip(specs, ref_out)) and status == [vt.OK] * len(specs)
     plan.close()
+    # every job's batched grid against the oracle's grid of the same mesh and resolution
+    import oracle
+
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle_ok = 0
+    for j, sp in zip(jobs, specs):
+        ref = oracle.voxelize(j.verts, j.tets, j.origin, j.voxel_size, j.res)
+        oracle_ok += int(np.array_equal(sp.out.cpu().numpy().view(np.uint32), ref))
+    oracle_s = time.perf_counter() - t0
     bmean, smean = statistics.mean(b_ms), statistics.mean(s_ms)
     q = lambda xs, f: float(np.percentile(np.asarray(xs), f))
     return {
@@ -363,6 +373,7 @@ def batched_section(args, flush, stream):
         "speedup_jobs_per_s": smean / bmean,
         "span_rows_by_res": {str(r): v["span_rows"] for r, v in tuned.items()},
         "bit_identical": exact,
+        "oracle_exact": f"{oracle_ok}/{len(specs)}", "oracle_s": oracle_s, "oracle_threads": oracle.last_threads(),
     }
 
 
@@ -734,6 +745,7 @@ def run_ours(args):
     # the launches the library's profile events bracket
     main_kernel = ("k_slices + k_voxelize (list pass over the tets the slice-unit kernel leaves)"
                    if kernel == 2 else "k_voxelize")
+    traffic_kernel = "k_slices" if kernel == 2 else "k_voxelize"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -757,10 +769,10 @@ def run_ours(args):
         "gpu_launches": int(launches),
         # the kernel is bound by issued lane operations, not by HBM: its primary roofline is the
         # ALU one; the HBM fraction (algorithmic bytes over the measured copy bandwidth) is kept beside it
-        "roofline": dict(alu_roofline(int(stats["rows"]), n_t, kmean), traffic=recorded_traffic(args.workload),
+        "roofline": dict(alu_roofline(int(stats["rows"]), n_t, kmean), traffic=recorded_traffic(args.workload, traffic_kernel),
                          kernel=main_kernel, kernel_ms=kmean),
         "hbm_roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                         "traffic": recorded_traffic(args.workload), "kernel": main_kernel, "kernel_ms": kmean,
+                         "traffic": recorded_traffic(args.workload, traffic_kernel), "kernel": main_kernel, "kernel_ms": kmean,
                          "algorithmic_bytes": alg_bytes, "peak_source": peak_kind},
         "stats": {"rows": int(stats["rows"]), "spans": int(stats["spans"]),
                   "fallback_rows": int(stats["fallback_rows"]), "degenerate_tets": int(stats["degenerate_tets"]),

@@ -112,3 +112,60 @@ def test_slab_cuts_cover_and_balance():
     assert max(shares) == 5.0 and min(shares) == 5.0
     with pytest.raises(ValueError):
         slabs.slab_cuts(5, 0)
+
+
+def _slab_rank_gpu_main(rank, world, port, q):
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import oracle
+    from paper_2106_01326_gb300 import meshgen as mg
+    from paper_2106_01326_gb300 import slabs
+    from paper_2106_01326_gb300 import voxtet as vt
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    v, t = mg.clipped_kuhn_lattice(16, 0.25, 21, mg.torus_sdf(0.3, 0.12))
+    res3, h = (200, 180, 220), 1.0 / 220
+    w = slabs.slice_weights(v, t, (0, 0, 0), h, res3[2])
+    z0, z1 = slabs.rank_slab(res3[2], rank, world, w)
+    sv, st = slabs.slab_mesh(v, t, (0, 0, 0), h, z0, z1)  # this rank's tets and only their vertices
+    out = []
+    for kernel in (vt.KERNEL_SPANS, vt.KERNEL_SLICES):
+        g = vt.voxelize_grid(torch.from_numpy(sv).cuda(), torch.from_numpy(st).cuda(), (0, 0, 0), h, res3,
+                             z_range=(z0, z1), kernel=kernel)
+        out.append(g.cpu().numpy().view(np.uint32))
+    got = [None] * world
+    dist.all_gather_object(got, (z0, z1, out[0], out[1]))
+    dist.destroy_process_group()
+    full = oracle.voxelize_grid(v, t, (0, 0, 0), h, res3)
+    parts = sorted(got, key=lambda x: x[0])
+    ok = [bool((np.concatenate([p[2 + k] for p in parts], axis=0) == full).all()) for k in range(2)]
+    q.put((rank, (z0, z1), ok))
+
+
+@pytest.mark.gpu
+def test_two_gloo_ranks_cuda_slabs_concatenate_to_oracle_grid():
+    """Each of two gloo ranks voxelizes its weighted z-slab through the CUDA path (both work
+    distributions) from its own compacted mesh; the gathered slabs equal the oracle's whole grid."""
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    from paper_2106_01326_gb300 import build as vbuild
+
+    vbuild.build()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_slab_rank_gpu_main, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=300) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert all(all(ok) for _, _, ok in out), out
+    (a0, a1), (b0, b1) = out[0][1], out[1][1]
+    assert a0 == 0 and a1 == b0 and b1 == 220 and 0 < a1 < 220
