@@ -21,12 +21,13 @@ def test_alu_roofline_counts_and_peak():
 
 
 def test_recorded_traffic_only_for_matching_sources(monkeypatch):
-    rec = bench.recorded_traffic("sliver_60")
+    rec = bench.recorded_traffic("sliver_60", "k_slices")
     if rec is not None:  # the committed capture matches the committed sources
         assert rec > 40_000_000
-    assert bench.recorded_traffic("torus_48") is None  # another workload
+    assert bench.recorded_traffic("torus_48", "k_slices") is None  # another workload
+    assert bench.recorded_traffic("sliver_60", "k_nonexistent") is None  # no capture of that kernel
     monkeypatch.setattr(bench, "kernel_source_digest", lambda: "0" * 64)
-    assert bench.recorded_traffic("sliver_60") is None  # sources changed since the capture
+    assert bench.recorded_traffic("sliver_60", "k_slices") is None  # sources changed since the capture
 
 
 def test_alu_roofline_counts_rows_with_samples_when_known():
