@@ -88,8 +88,9 @@ typedef struct {
 
 /* Counters the last call on a workspace left in it (read with voxtet_read_stats). */
 typedef struct {
-    uint64_t spans;           /* work items (tet, run of x-rows) distributed to threads */
-    uint64_t rows;            /* x-rows solved by the single-precision filter */
+    uint64_t spans;           /* work items distributed to threads: (tet, run of z-slices) spans, or
+                                 (tet, z-slice) units with the slice-unit distribution */
+    uint64_t rows;            /* candidate x-rows solved by the single-precision filter */
     uint64_t fallback_rows;   /* rows the filter could not certify (re-solved with exact integers) */
     uint64_t degenerate_tets; /* tetrahedra with zero signed volume (skipped) */
     uint64_t wide_tets;       /* tetrahedra wider than 2^20 lattice units (128-bit exact path) */
