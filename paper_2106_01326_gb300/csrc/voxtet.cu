@@ -1104,7 +1104,12 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
     if (o.profile && profile_begin(stream) != cudaSuccess) return VOXTET_ERR_CUDA;
     if (use_slice_units(o, g)) {
       // slice units for the tets that fit them, then the span kernel over the tets it listed
-      if (launch_slices(p, variant, dev->sms, stream) != VOXTET_OK) return VOXTET_ERR_CUDA;
+      // 16 slices per tet (7 blocks per SM) up to 512 voxels per side, where a tet of a mesh
+      // fine enough for the grid spans a few slices (sliver mesh: at most 13), 32 above
+      // (measured on GB300, sliver mesh 512^3: 308 -> 285 us with 16); a tet spanning more
+      // goes to the list pass either way
+      const int cap = g.longest() <= 512 ? kSuSlicesSmall : kSuSlices;
+      if (launch_slices(p, variant, cap, dev->sms, stream) != VOXTET_OK) return VOXTET_ERR_CUDA;
       g_launches.fetch_add(1);
       Params q = p;
       q.list_mode = 1;

@@ -34,12 +34,11 @@ namespace voxtet {
 constexpr int kSuWarps = kSuBlock / 32;
 constexpr int kSuBuckets = 64;                           // row counts 1..63 one bucket each, >= 64 together
 constexpr int kSuCounters = kSuBuckets * kSuWarps;       // bucket-major, one counter per warp of each bucket
-constexpr int kSuCap = kSuBlock * kSuSlices;             // most units of one tile
 constexpr int kSuRec = 28;  // floats per tet record: 24 used; 7 groups of 16 bytes, an odd number,
                             // so that lanes loading records of random slots spread over all banks
 constexpr int kSuStage = 64;                             // staged uncertain rows per block (about 5 per tile)
 constexpr uint32_t kSuEmpty = 0xFFFFFFFFu;               // a slice without candidate rows
-static_assert(kSuBlock == 128 && kSuSlices == 32 && kSuRows == 1024, "unit fields: 7 + 5 bits; rows in 10 bits");
+static_assert(kSuBlock == 128 && kSuSlices <= 32 && kSuRows == 1024, "unit fields: 7 + 5 bits; rows in 10 bits");
 
 // Tet record (kSuRec floats per slot).  The faces bounding a from above (Dx < 0) fill slots
 // U0..U2 and those bounding it from below (Dx > 0) slots L0..L2, unused slots a neutral face
@@ -49,13 +48,14 @@ static_assert(kSuBlock == 128 && kSuSlices == 32 && kSuRows == 1024, "unit field
 // offset of the box's row (b, c) = (0, 0).
 constexpr int kRecAl = 0, kRecBe = 6, kRecGa = 12, kRecDU = 18, kRecDL = 19, kRecHi = 20, kRecI0 = 21, kRecBase = 22;
 
-// Shared memory of one block (dynamic).
+// Shared memory of one block (dynamic), for tets of at most SL slices.
+template <int SL>
 struct SuSmem {
   float rec[kSuBlock * kSuRec];
   // per tet slot, slice k of its tet: b_lo | (n - 1) << 10, or kSuEmpty
-  uint32_t slice[kSuSlices][kSuBlock];
+  uint32_t slice[SL][kSuBlock];
   // the tile's units sorted by row count, longest first: slot | k << 7
-  uint16_t unit[kSuCap];
+  uint16_t unit[kSuBlock * SL];
   uint32_t hist[kSuCounters];
   uint32_t cur[kSuCounters + 1];
   uint32_t warp_tot[kSuWarps];
@@ -63,7 +63,9 @@ struct SuSmem {
   long long tile;
 };
 
-static_assert(sizeof(SuSmem) <= 44 * 1024, "slice-unit kernel shared memory: five blocks per SM");
+// 16-slice tiles fit 7 blocks per SM (228 KB, 1 KB reserved per block), 32-slice tiles 5
+static_assert(sizeof(SuSmem<kSuSlicesSmall>) <= 31 * 1024, "slice-unit kernel shared memory: seven blocks per SM");
+static_assert(sizeof(SuSmem<kSuSlices>) <= 44 * 1024, "slice-unit kernel shared memory: five blocks per SM");
 
 // Counter of a unit with n rows emitted by warp w: longer units first.
 __device__ __forceinline__ int su_counter(int n, int w) {
@@ -136,8 +138,8 @@ __device__ __forceinline__ void su_rows(const SuEdges &E, int Z, int s, int sh, 
 // Phase (1) for tet t of this thread (t < 0: none).  Returns the slices whose entries it
 // wrote to sm.slice (0 if the tet has no unit here); counts each unit in its counter (no
 // rank is needed here, so the count does not wait on the shared-memory atomic).
-template <bool STRICT, bool CULL>
-__device__ __forceinline__ int su_setup(const Params &p, long long t, SuSmem &sm, TileCounters &ctr) {
+template <bool STRICT, bool CULL, int SL>
+__device__ __forceinline__ int su_setup(const Params &p, long long t, SuSmem<SL> &sm, TileCounters &ctr) {
   const int tid = threadIdx.x, warp = tid >> 5;
   if (t < 0) return 0;
   int3 V[4];
@@ -174,7 +176,7 @@ __device__ __forceinline__ int su_setup(const Params &p, long long t, SuSmem &sm
     p.tetq[k] = (uint32_t)t;
     return 0;
   }
-  if (bx.nc > kSuSlices || bx.nb > kSuRows) {  // the span kernel takes it (list mode)
+  if (bx.nc > SL || bx.nb > kSuRows) {  // the span kernel takes it (list mode)
     const unsigned k = atomicAdd(&p.hdr->listq_count, 1u);
     p.tetq[p.n_tets - 1 - k] = (uint32_t)t;
     return 0;
@@ -295,7 +297,8 @@ __device__ __forceinline__ int su_setup(const Params &p, long long t, SuSmem &sm
 
 // Block-wide exclusive prefix sum of one value per thread (all threads call it); `total`
 // gets the sum.  Uses sm.warp_tot; ends with the block in step.
-__device__ __forceinline__ uint32_t su_block_scan(SuSmem &sm, uint32_t v, uint32_t &total) {
+template <int SL>
+__device__ __forceinline__ uint32_t su_block_scan(SuSmem<SL> &sm, uint32_t v, uint32_t &total) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   uint32_t x = v;
 #pragma unroll
@@ -364,8 +367,8 @@ __device__ __forceinline__ bool su_row(const SuUnit &u, float bf, uint32_t *row)
 }
 
 // Phase (3): rows b0 .. b0 + n - 1 of slice k of the tet in `slot` (tet index t).
-template <bool STRICT, bool CLAMP>
-__device__ __forceinline__ void su_walk(const Params &p, SuSmem &sm, int slot, long long t, int k, int b0, int n) {
+template <bool STRICT, bool CLAMP, int SL>
+__device__ __forceinline__ void su_walk(const Params &p, SuSmem<SL> &sm, int slot, long long t, int k, int b0, int n) {
   const float4 *R = reinterpret_cast<const float4 *>(sm.rec + slot * kSuRec);
   const float4 q0 = R[0], q1 = R[1], q2 = R[2], q3 = R[3], q4 = R[4], q5 = R[5];
   const float cf = (float)k;
@@ -403,10 +406,10 @@ __device__ __forceinline__ void su_walk(const Params &p, SuSmem &sm, int slot, l
   }
 }
 
-template <bool STRICT, bool CULL, bool CLAMP, bool STRIDED>
-__global__ void __launch_bounds__(kSuBlock, 5) k_slices(Params p) {
+template <bool STRICT, bool CULL, bool CLAMP, bool STRIDED, int SL>
+__global__ void __launch_bounds__(kSuBlock, SL == kSuSlicesSmall ? 7 : 5) k_slices(Params p) {
   extern __shared__ __align__(16) unsigned char su_dyn_smem[];
-  SuSmem &sm = *reinterpret_cast<SuSmem *>(su_dyn_smem);
+  SuSmem<SL> &sm = *reinterpret_cast<SuSmem<SL> *>(su_dyn_smem);
   const int tid = threadIdx.x;
   TileCounters ctr;
   for (int i = tid; i < kSuCounters; i += kSuBlock) sm.hist[i] = 0u;
@@ -427,7 +430,7 @@ __global__ void __launch_bounds__(kSuBlock, 5) k_slices(Params p) {
     }
     if (t >= p.n_tets) t = -1;
     // (1) set up this thread's tet and its slices' row ranges; count units per counter
-    const int nc = su_setup<STRICT, CULL>(p, t, sm, ctr);
+    const int nc = su_setup<STRICT, CULL, SL>(p, t, sm, ctr);
     __syncthreads();
     // (2) exclusive scan of the counters (two per thread) into cursors, then every unit to
     // its place (a cursor per counter: units of one counter come from one warp)
@@ -461,7 +464,7 @@ __global__ void __launch_bounds__(kSuBlock, 5) k_slices(Params p) {
       const int b0 = (int)(e & 1023u), n = (int)(e >> 10) + 1;
       const long long tt = STRIDED ? base + (long long)slot * p.tile_stride : base + slot;
       ctr.rows += (unsigned)n;
-      su_walk<STRICT, CLAMP>(p, sm, slot, tt, k, b0, n);
+      su_walk<STRICT, CLAMP, SL>(p, sm, slot, tt, k, b0, n);
     }
     flush_stage(p, sm.stage);
   }
@@ -472,46 +475,51 @@ __global__ void __launch_bounds__(kSuBlock, 5) k_slices(Params p) {
 
 typedef void (*SuKernel)(Params);
 
+template <int SL>
 static SuKernel su_kernel(int v) {
   switch (v) {
-    case 0: return k_slices<false, false, false, false>;
-    case 1: return k_slices<false, false, true, false>;
-    case 2: return k_slices<false, true, false, false>;
-    case 3: return k_slices<false, true, true, false>;
-    case 4: return k_slices<true, false, false, false>;
-    case 5: return k_slices<true, false, true, false>;
-    case 6: return k_slices<true, true, false, false>;
-    case 7: return k_slices<true, true, true, false>;
-    case 8: return k_slices<false, false, false, true>;
-    case 9: return k_slices<false, false, true, true>;
-    case 10: return k_slices<false, true, false, true>;
-    case 11: return k_slices<false, true, true, true>;
-    case 12: return k_slices<true, false, false, true>;
-    case 13: return k_slices<true, false, true, true>;
-    case 14: return k_slices<true, true, false, true>;
-    default: return k_slices<true, true, true, true>;
+    case 0: return k_slices<false, false, false, false, SL>;
+    case 1: return k_slices<false, false, true, false, SL>;
+    case 2: return k_slices<false, true, false, false, SL>;
+    case 3: return k_slices<false, true, true, false, SL>;
+    case 4: return k_slices<true, false, false, false, SL>;
+    case 5: return k_slices<true, false, true, false, SL>;
+    case 6: return k_slices<true, true, false, false, SL>;
+    case 7: return k_slices<true, true, true, false, SL>;
+    case 8: return k_slices<false, false, false, true, SL>;
+    case 9: return k_slices<false, false, true, true, SL>;
+    case 10: return k_slices<false, true, false, true, SL>;
+    case 11: return k_slices<false, true, true, true, SL>;
+    case 12: return k_slices<true, false, false, true, SL>;
+    case 13: return k_slices<true, false, true, true, SL>;
+    case 14: return k_slices<true, true, false, true, SL>;
+    default: return k_slices<true, true, true, true, SL>;
   }
 }
 
 constexpr int kSuMaxDevices = 64;
-static int g_su_occ[kSuMaxDevices][16];  // resident blocks per SM per variant, 0 = not yet queried
+static int g_su_occ[kSuMaxDevices][2][16];  // resident blocks per SM per capacity and variant, 0 = not yet queried
 static std::atomic<int> g_su_lock{0};
 
-size_t slices_smem_bytes() { return sizeof(SuSmem); }
+size_t slices_smem_bytes(int slices) {
+  return slices <= kSuSlicesSmall ? sizeof(SuSmem<kSuSlicesSmall>) : sizeof(SuSmem<kSuSlices>);
+}
 
-int launch_slices(const Params &p_in, int variant, int sms, cudaStream_t stream) {
+int launch_slices(const Params &p_in, int variant, int slices, int sms, cudaStream_t stream) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kSuMaxDevices) return VOXTET_ERR_CUDA;
-  SuKernel kern = su_kernel(variant & 15);
-  int occ = g_su_occ[dev][variant & 15];
+  const int c = slices <= kSuSlicesSmall ? 0 : 1;
+  SuKernel kern = c == 0 ? su_kernel<kSuSlicesSmall>(variant & 15) : su_kernel<kSuSlices>(variant & 15);
+  const size_t smem = slices_smem_bytes(slices);
+  int occ = g_su_occ[dev][c][variant & 15];
   if (occ == 0) {
     while (g_su_lock.exchange(1)) {
     }
     cudaError_t e = cudaFuncSetAttribute(reinterpret_cast<const void *>(kern),
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SuSmem));
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSuBlock, sizeof(SuSmem));
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kSuBlock, smem);
     if (e == cudaSuccess && occ < 1) occ = 1;
-    if (e == cudaSuccess) g_su_occ[dev][variant & 15] = occ;
+    if (e == cudaSuccess) g_su_occ[dev][c][variant & 15] = occ;
     g_su_lock.store(0);
     if (e != cudaSuccess) return VOXTET_ERR_CUDA;
   }
@@ -528,7 +536,7 @@ int launch_slices(const Params &p_in, int variant, int sms, cudaStream_t stream)
   }
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kSuBlock, sizeof(SuSmem), stream>>>(p);
+  kern<<<(unsigned)grid, kSuBlock, smem, stream>>>(p);
   return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
 }
 
