@@ -115,26 +115,6 @@ __device__ __forceinline__ void su_edges(const int3 V[4], SuEdges &E) {
   E.z2 = z[2];
 }
 
-// Candidate rows [b_lo, b_hi] of the slice at height Z from its crossing points on the
-// edges listed (the cross-section's y-extent widened by 2 lattice units, in rows).
-template <int A, int B, int C, int D>
-__device__ __forceinline__ void su_rows(const SuEdges &E, int Z, int s, int sh, int j0, int nb, int &b_lo, int &b_hi) {
-  const float Zf = (float)Z;
-  const float ya = __fmaf_rn(Zf - E.zp[A], E.k[A], E.yp[A]);
-  const float yb = __fmaf_rn(Zf - E.zp[B], E.k[B], E.yp[B]);
-  const float yc = __fmaf_rn(Zf - E.zp[C], E.k[C], E.yp[C]);
-  float ymin = fminf(ya, fminf(yb, yc)), ymax = fmaxf(ya, fmaxf(yb, yc));
-  if (D >= 0) {  // the slices in [z1, z2]: four edges, and vertex 2 itself at Z = z2
-    const float yd = __fmaf_rn(Zf - E.zp[D], E.k[D], E.yp[D]);
-    const float y2 = Z == E.z2 ? E.yp[5] : yd;
-    ymin = fminf(ymin, fminf(yd, y2));
-    ymax = fmaxf(ymax, fmaxf(yd, y2));
-  }
-  const int ylo = (int)floorf(ymin) - 2, yhi = (int)ceilf(ymax) + 2;
-  b_lo = max(((ylo + s - 1) >> sh) - j0, 0);
-  b_hi = min(((yhi - s) >> sh) - j0, nb - 1);
-}
-
 // Phase (1) for tet t of this thread (t < 0: none).  Returns the slices whose entries it
 // wrote to sm.slice (0 if the tet has no unit here); counts each unit in its counter (no
 // rank is needed here, so the count does not wait on the shared-memory atomic).
@@ -282,11 +262,26 @@ __device__ __forceinline__ int su_setup(const Params &p, long long t, SuSmem<SL>
   if (CULL) {
     const int step = 1 << p.sh;
     int Z = s + (bx.l0 << p.sh);
+    // the edges' first end points are vertices 0 (01 02 03), 1 (12 13) and 2 (23)
+    const float zs0 = EG.zp[0], zs1 = EG.zp[3], zs2 = EG.zp[5], ys0 = EG.yp[0], ys1 = EG.yp[3], ys2 = EG.yp[5];
+    const float k0 = EG.k[0], k1 = EG.k[1], k2 = EG.k[2], k3 = EG.k[3], k4 = EG.k[4], k5 = EG.k[5];
     for (int k = 0; k < bx.nc; ++k, Z += step) {
-      int b_lo, b_hi;
-      if (k < kA) su_rows<0, 1, 2, -1>(EG, Z, s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
-      else if (k < kB) su_rows<1, 2, 3, 4>(EG, Z, s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
-      else su_rows<2, 4, 5, -1>(EG, Z, s, p.sh, bx.j0, bx.nb, b_lo, b_hi);
+      // the slice's crossing points, edges chosen by selects (one straight-line body for all
+      // slices): below z1 03 01 02; in [z1, z2] 03 02 12 13 and vertex 2 at z2; above 03 13 23
+      const float Zf = (float)Z;
+      const bool pa = k < kA, pb = !pa && k < kB, pc = !pa && !pb;
+      const float d0 = Zf - zs0, d1 = Zf - zs1, d2 = Zf - zs2;
+      const float y1 = __fmaf_rn(d0, k2, ys0);
+      const float y2 = __fmaf_rn(pc ? d1 : d0, pa ? k0 : (pb ? k1 : k4), pc ? ys1 : ys0);
+      const float y3 = __fmaf_rn(pa ? d0 : (pb ? d1 : d2), pa ? k1 : (pb ? k3 : k5), pa ? ys0 : (pb ? ys1 : ys2));
+      const float y4 = pb ? __fmaf_rn(d1, k4, ys1) : y1;
+      const float y5 = pb && Z == EG.z2 ? ys2 : y1;
+      const float ymin = fminf(fminf(fminf(y1, y2), fminf(y3, y4)), y5);
+      const float ymax = fmaxf(fmaxf(fmaxf(y1, y2), fmaxf(y3, y4)), y5);
+      // the y-extent widened by 2 lattice units, in rows
+      const int ylo = (int)floorf(ymin) - 2, yhi = (int)ceilf(ymax) + 2;
+      const int b_lo = max(((ylo + s - 1) >> p.sh) - bx.j0, 0);
+      const int b_hi = min(((yhi - s) >> p.sh) - bx.j0, bx.nb - 1);
       emit(k, b_lo, b_hi);
     }
   } else {
