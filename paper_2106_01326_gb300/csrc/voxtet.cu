@@ -51,6 +51,7 @@ namespace voxtet {
 
 __global__ void k_prologue(Header *hdr, uint32_t *redo, long long redo_words, uint32_t *out, long long n_words,
                            int clear) {
+  chain_release();  // the snap kernel may be scheduled now; it waits for this one to complete
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   const long long stride = (long long)gridDim.x * blockDim.x;
   if (tid < 64) reinterpret_cast<uint32_t *>(hdr)[tid] = 0u;
@@ -75,6 +76,8 @@ __global__ void k_prologue(Header *hdr, uint32_t *redo, long long redo_words, ui
 // pipe instead of GB300's narrow FP64 unit.
 __global__ void k_snap(const float *__restrict__ v, long long n, double ox, double oy, double oz, double h,
                        double scale, double mul, int use_mul, int fast, int4 *__restrict__ out, Header *hdr) {
+  chain_wait();  // the prologue has zeroed the header
+  chain_release();
   const long long stride = (long long)gridDim.x * blockDim.x;
   int err = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -116,6 +119,8 @@ __global__ void k_snap(const float *__restrict__ v, long long n, double ox, doub
 }
 
 __global__ void k_load_fixed(const int *__restrict__ xyz, long long n, int4 *__restrict__ out, Header *hdr) {
+  chain_wait();  // the prologue has zeroed the header
+  chain_release();
   const long long stride = (long long)gridDim.x * blockDim.x;
   int err = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
@@ -573,6 +578,8 @@ __device__ __forceinline__ uint32_t (*dynamic_slice_table())[kBlock] {
 
 template <bool STRICT, bool CULL, bool CLAMP, bool STRIDED>
 __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS) k_voxelize(Params p) {
+  chain_wait();  // vertices snapped, header zeroed; in list mode the slice-unit kernel has listed its tets
+  chain_release();
   __shared__ TileSmem sm;
   uint32_t (*const slice_tab)[kBlock] = dynamic_slice_table();
   __shared__ unsigned long long tile_s;
@@ -665,6 +672,7 @@ __device__ __forceinline__ void exact_job(const Params &p) {
 
 template <bool STRICT>
 __global__ void __launch_bounds__(128) k_exact(Params p) {
+  chain_wait();  // every row and tet is queued
   exact_job<STRICT>(p);
 }
 
@@ -1118,9 +1126,13 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
       // one block per SM: the list is usually empty or short (tets spanning more than 32
       // slices or 1024 rows per slice), and an empty list then costs one short wave
       const int lv = variant & 7;
-      voxelize_kernel(lv)<<<(unsigned)dev->sms, kBlock, slice_table_bytes(q.max_slices), stream>>>(q);
+      if (launch_chained(voxelize_kernel(lv), (unsigned)dev->sms, kBlock, slice_table_bytes(q.max_slices), stream,
+                         q) != cudaSuccess)
+        return VOXTET_ERR_CUDA;
     } else {
-      voxelize_kernel(variant)<<<(unsigned)grid, kBlock, slice_table_bytes(p.max_slices), stream>>>(p);
+      if (launch_chained(voxelize_kernel(variant), (unsigned)grid, kBlock, slice_table_bytes(p.max_slices), stream,
+                         p) != cudaSuccess)
+        return VOXTET_ERR_CUDA;
     }
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
@@ -1129,8 +1141,8 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
       t_prof.pending = true;
     }
     const unsigned eg = (unsigned)dev->sms * 4;
-    if (o.mode == 1) k_exact<true><<<eg, kExactBlock, 0, stream>>>(p);
-    else k_exact<false><<<eg, kExactBlock, 0, stream>>>(p);
+    if (launch_chained(o.mode == 1 ? k_exact<true> : k_exact<false>, eg, kExactBlock, 0, stream, p) != cudaSuccess)
+      return VOXTET_ERR_CUDA;
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
   }
@@ -1198,9 +1210,10 @@ static int launch_snap(const Workspace &w, const float *d_verts, long long n_ver
   const double mul = use_mul ? std::ldexp(1.0, kLatticeBits - K - (e2 - 1)) : 0.0;
   const int fast = use_mul && mul >= 1.0 && mul <= 0x1p100 && grid_origin[0] == 0.0f && grid_origin[1] == 0.0f &&
                    grid_origin[2] == 0.0f;
-  k_snap<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(
-      d_verts, n_verts, (double)grid_origin[0], (double)grid_origin[1], (double)grid_origin[2], h, scale, mul,
-      use_mul, fast, w.verts4, w.hdr);
+  if (launch_chained(k_snap, (unsigned)grid_blocks(n_verts, 256, dev->sms), 256, 0, stream, d_verts, n_verts,
+                     (double)grid_origin[0], (double)grid_origin[1], (double)grid_origin[2], h, scale, mul, use_mul,
+                     fast, w.verts4, w.hdr) != cudaSuccess)
+    return VOXTET_ERR_CUDA;
   g_launches.fetch_add(1);
   return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
 }
@@ -1316,7 +1329,9 @@ int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   if (n_verts > 0) {
-    k_load_fixed<<<grid_blocks(n_verts, 256, dev->sms), 256, 0, stream>>>(d_xyz, n_verts, w.verts4, w.hdr);
+    if (launch_chained(k_load_fixed, (unsigned)grid_blocks(n_verts, 256, dev->sms), 256, 0, stream, d_xyz, n_verts,
+                       w.verts4, w.hdr) != cudaSuccess)
+      return VOXTET_ERR_CUDA;
     g_launches.fetch_add(1);
     if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
   }

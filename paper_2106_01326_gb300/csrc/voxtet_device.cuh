@@ -88,6 +88,34 @@ static unsigned long long row_queue_capacity(long long n_tets) {
 }
 
 
+// ------------------------------------------------------------------ chained launches
+//
+// The kernels of one call run back to back on one stream.  Each after the first is launched
+// as a programmatic dependent of the one before it (launch_chained), so that its blocks are
+// scheduled while the previous kernel drains instead of after it; every such kernel calls
+// chain_wait() before it touches memory, which returns once the previous kernel has completed
+// and its writes are visible (at once for a kernel launched the ordinary way).  chain_release()
+// lets the next kernel's launch begin; it orders nothing, the next kernel's chain_wait() does.
+
+__device__ __forceinline__ void chain_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void chain_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... Args, typename... Actual>
+static cudaError_t launch_chained(void (*kernel)(Args...), unsigned grid, unsigned block, size_t smem,
+                                  cudaStream_t stream, Actual &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<Actual &&>(args)...);
+}
+
 // ------------------------------------------------------------------ OR writes
 
 // OR the samples x0..x1 (inclusive, absolute x indices) into one row of words.

@@ -403,6 +403,8 @@ __device__ __forceinline__ void su_walk(const Params &p, SuSmem<SL> &sm, int slo
 
 template <bool STRICT, bool CULL, bool CLAMP, bool STRIDED, int SL>
 __global__ void __launch_bounds__(kSuBlock, SL == kSuSlicesSmall ? 7 : 5) k_slices(Params p) {
+  chain_wait();  // vertices snapped, header zeroed
+  chain_release();
   extern __shared__ __align__(16) unsigned char su_dyn_smem[];
   SuSmem<SL> &sm = *reinterpret_cast<SuSmem<SL> *>(su_dyn_smem);
   const int tid = threadIdx.x;
@@ -531,8 +533,7 @@ int launch_slices(const Params &p_in, int variant, int slices, int sms, cudaStre
   }
   if (grid > tiles) grid = tiles;
   if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kSuBlock, smem, stream>>>(p);
-  return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
+  return launch_chained(kern, (unsigned)grid, kSuBlock, smem, stream, p) == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
 }
 
 }  // namespace voxtet
