@@ -256,6 +256,45 @@ __device__ __forceinline__ bool exact_row(const Exact<T> &X, int nup, int nlo, i
   return true;
 }
 
+// The same interval as exact_row for a 64-bit tet, faces in any order (no slot order
+// needed).  Each bound starts from a single-precision estimate of the root of
+// lam(a) = H + Dx a, clamped to the box, and is then moved to the exact bound by exact
+// probes: lam is monotone in a, so stepping while the test still fails (or still holds one
+// step further) ends on the bound whatever the estimate; with the estimate within one of
+// the root, one or two probes per face.  Probes stay in [0, na-1] like the bisection's.
+template <bool STRICT>
+__device__ __forceinline__ bool exact_row_probe(const Exact<i64> &X, int na, int b, int c, int &lo_out,
+                                                int &hi_out) {
+  int lo = 0, hi = na - 1;
+  bool empty = false;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const i64 H = X.L[m] + X.Dz[m] * (i64)c + X.Dy[m] * (i64)b;
+    const i64 Dx = X.Dx[m];
+    if (Dx == 0) {
+      empty |= !lam_ok<STRICT>(H);
+      continue;
+    }
+    const float r = fminf(fmaxf(__fdividef(-__ll2float_rn(H), __ll2float_rn(Dx)), -1.f), (float)na);
+    int x = (int)floorf(r);  // in [-1, na]
+    if (Dx < 0) {  // lam decreasing in a: largest a in [-1, na-1] with lam(a) ok
+      x = min(x, na - 1);
+      while (x >= 0 && !lam_ok<STRICT>(H + Dx * (i64)x)) --x;
+      while (x + 1 <= na - 1 && lam_ok<STRICT>(H + Dx * (i64)(x + 1))) ++x;
+      hi = min(hi, x);
+    } else {  // lam increasing in a: smallest a in [0, na] with lam(a) ok
+      x = max(x, 0);
+      while (x <= na - 1 && !lam_ok<STRICT>(H + Dx * (i64)x)) ++x;
+      while (x - 1 >= 0 && lam_ok<STRICT>(H + Dx * (i64)(x - 1))) --x;
+      lo = max(lo, x);
+    }
+  }
+  if (empty || lo > hi) return false;
+  lo_out = lo;
+  hi_out = hi;
+  return true;
+}
+
 // Single-precision filter data of one 64-bit-exact tet, slot order as in Exact.
 // For slot m with Dx != 0, the real root of lam_m along the row is
 //   a*(b, c) = -(L + Dy b + Dz c) / Dx,

@@ -639,14 +639,10 @@ __device__ __forceinline__ void exact_tet(const Params &p, long long t) {
   else exact_tet_rows<STRICT, i128>(p, V, bx);
 }
 
-// The exact work of one mesh: its queued tets (a block each), queued rows (a thread
-// each) and, after a row-queue overflow, the tets flagged in its redo bitmap.
+// The queued rows of one mesh (a thread each).
 template <bool STRICT>
-__device__ __forceinline__ void exact_job(const Params &p) {
-  const unsigned n_tq = min((unsigned long long)p.hdr->tetq_count, (unsigned long long)p.n_tets);
-  const unsigned n_rq_all = p.hdr->rowq_count;
-  const unsigned n_rq = min(n_rq_all, p.q_cap);
-  for (unsigned q = blockIdx.x; q < n_tq; q += gridDim.x) exact_tet<STRICT>(p, p.tetq[q]);
+__device__ __forceinline__ void exact_rows_job(const Params &p) {
+  const unsigned n_rq = min(p.hdr->rowq_count, p.q_cap);
   const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
   for (unsigned i = gtid; i < n_rq; i += gsz) {
     const RowItem it = p.rowq[i];
@@ -655,25 +651,45 @@ __device__ __forceinline__ void exact_job(const Params &p) {
     oriented_tet(p, it.tet, V, bx);
     Exact<i64> X;
     exact_setup<i64>(V, bx, p.sh, X);
-    int slot[4], nup = 0, nlo = 0;
-    slot_order<i64>(X, slot, nup, nlo);
-    permute_slots<i64>(X, slot);
     int lo, hi;
-    if (exact_row<STRICT, i64>(X, nup, nlo, bx.na, it.b, it.c, lo, hi)) {
+    if (exact_row_probe<STRICT>(X, bx.na, it.b, it.c, lo, hi)) {
       uint32_t *row = p.out + ((size_t)(bx.l0 - p.z0 + it.c) * p.ry + (bx.j0 + it.b)) * p.W;
       or_span(row, bx.i0 + lo, bx.i0 + hi);
     }
   }
-  if (n_rq_all > p.q_cap) {
+}
+
+// The rest of the exact work of one mesh: its queued tets (a block each) and, after a
+// row-queue overflow, the tets flagged in its redo bitmap.
+template <bool STRICT>
+__device__ __forceinline__ void exact_tets_job(const Params &p) {
+  const unsigned n_tq = min((unsigned long long)p.hdr->tetq_count, (unsigned long long)p.n_tets);
+  for (unsigned q = blockIdx.x; q < n_tq; q += gridDim.x) exact_tet<STRICT>(p, p.tetq[q]);
+  if (p.hdr->rowq_count > p.q_cap) {
     for (long long t = blockIdx.x; t < p.n_tets; t += gridDim.x)
       if ((p.redo[t >> 5] >> (t & 31)) & 1u) exact_tet<STRICT>(p, t);
   }
 }
 
 template <bool STRICT>
+__device__ __forceinline__ void exact_job(const Params &p) {
+  exact_tets_job<STRICT>(p);
+  exact_rows_job<STRICT>(p);
+}
+
+// The queued rows, in a kernel of their own: the 64-bit row solve needs far fewer registers
+// than the tet path's 128-bit one, so many more threads are resident.
+template <bool STRICT>
+__global__ void __launch_bounds__(128) k_exact_rows(Params p) {
+  chain_wait();  // every row is queued
+  chain_release();
+  exact_rows_job<STRICT>(p);
+}
+
+template <bool STRICT>
 __global__ void __launch_bounds__(128) k_exact(Params p) {
-  chain_wait();  // every row and tet is queued
-  exact_job<STRICT>(p);
+  chain_wait();  // every tet is queued
+  exact_tets_job<STRICT>(p);
 }
 
 // ------------------------------------------------------------------ batched kernels
@@ -885,6 +901,8 @@ static VoxKernel voxelize_kernel(int idx) {
 struct DeviceInfo {
   int sms = 0;
   int occ[kVariants] = {};  // resident blocks per SM of each k_voxelize variant
+  int occ_exact = 0;        // resident blocks per SM of the exact kernels (tets, rows)
+  int occ_rows = 0;
   bool ready = false;
 };
 static DeviceInfo g_dev[kMaxDevices];
@@ -935,6 +953,10 @@ static cudaError_t device_info(DeviceInfo *&out) {
           e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ[v], voxelize_kernel(v), kBlock,
                                                             kSliceTableBytesMax);
       }
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_exact, k_exact<false>, kExactBlock, 0);
+      if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.occ_rows, k_exact_rows<false>, kExactBlock, 0);
+      if (e == cudaSuccess && d.occ_exact < 1) d.occ_exact = 1;
+      if (e == cudaSuccess && d.occ_rows < 1) d.occ_rows = 1;
       if (e == cudaSuccess) d.ready = true;
     }
     g_dev_lock.store(0);
@@ -1140,7 +1162,13 @@ static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *te
       if (cudaEventRecord(t_prof.stop, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
       t_prof.pending = true;
     }
-    const unsigned eg = (unsigned)dev->sms * 4;
+    // one wave of resident blocks each: the queued rows are spread evenly over the threads
+    const unsigned rg = (unsigned)dev->sms * (unsigned)dev->occ_rows;
+    if (launch_chained(o.mode == 1 ? k_exact_rows<true> : k_exact_rows<false>, rg, kExactBlock, 0, stream, p) !=
+        cudaSuccess)
+      return VOXTET_ERR_CUDA;
+    g_launches.fetch_add(1);
+    const unsigned eg = (unsigned)dev->sms * (unsigned)dev->occ_exact;
     if (launch_chained(o.mode == 1 ? k_exact<true> : k_exact<false>, eg, kExactBlock, 0, stream, p) != cudaSuccess)
       return VOXTET_ERR_CUDA;
     g_launches.fetch_add(1);
