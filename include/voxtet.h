@@ -39,6 +39,15 @@
  *     rejected call returns a negative status and touches nothing.
  *   - Calls on different streams with disjoint workspaces and grids are
  *     independent.  Two in-flight calls sharing a workspace race.
+ *   - A call's first kernel is an ordinary launch, so everything enqueued on
+ *     `stream` before the call has completed when it starts; the call's later
+ *     kernels are programmatic dependents of the kernel before them and wait
+ *     for it on the device.  With opts->sync = 0 (and the workspace and grid
+ *     allocated beforehand) voxelize_tets, voxelize_tets_fixed and
+ *     voxelize_tets_grid take no host-side action between launches, so a
+ *     stream capture of such a call replays as the call, device-detected
+ *     errors included (read them from the workspace); make the first call on
+ *     a device outside any capture (it sets kernel attributes once).
  */
 #ifndef VOXTET_H
 #define VOXTET_H
