@@ -129,6 +129,27 @@ def test_coplanar_face_ties(vt, res, spread, n):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
+def test_filter_defers_ties_and_never_certifies_a_wrong_row(vt, mode):
+    """The single-precision filter on inputs built to defeat it (faces through many samples,
+    vertices at unaligned lattice points).  It must hand rows it cannot decide to the exact
+    kernels (fallback rows counted) and every row it certifies must agree with exact
+    arithmetic: the grid equals the exact-only grid and the oracle's."""
+    import torch
+
+    res = 256
+    xyz, tets = mg.coplanar_face_soup(2000, res, seed=4242 + mode, spread=30)
+    ref = oracle.voxelize_fixed(xyz, tets, res, mode=mode)
+    ws = vt.alloc_workspace(len(tets), len(xyz), res)
+    d_xyz, d_tets = _dev(xyz, torch.int32), _dev(tets.reshape(-1, 4), torch.int32)
+    got = vt.voxelize_fixed(d_xyz, d_tets, res, workspace=ws, mode=mode).cpu().numpy().view(np.uint32)
+    st = vt.read_stats(ws)
+    exact_only = vt.voxelize_fixed(d_xyz, d_tets, res, mode=mode, use_filter=False).cpu().numpy().view(np.uint32)
+    assert st["rows"] > 0 and 0 < st["fallback_rows"] < st["rows"], st
+    assert_same(got, ref, res, f"filter mode={mode}")
+    assert np.array_equal(got, exact_only)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
 def test_coplanar_face_ties_clamped_filter(vt, mode):
     """2048^3: the filter clamps each face's bracket to where the face can change a row; ties
     placed on planes through samples must still come out exact at the clamp boundaries."""
