@@ -11,8 +11,13 @@
 // Kernels (one stream, in order):
 //   k_prologue   zero the workspace header and redo bitmap, and (unless
 //                accumulating) the grid
-//   k_snap       float vertices -> lattice int4 (x, y, z, flag); k_load_fixed
+//   k_snap       float vertices -> lattice int4 (x, y, z, error bits); k_load_fixed
 //                does the range check for vertices already on the lattice
+//                (k_prep<FIXED> does the prologue and either in one launch for
+//                calls with tets; k_exact then reports the vertices' errors)
+//   k_slices     (voxtet_slices.cu) the same as k_voxelize with (tet, z-slice)
+//                units sorted by exact row count; k_voxelize then takes the tets
+//                it lists
 //   k_voxelize   persistent; each block repeatedly claims a tile of tets and
 //                (1) computes per tet the sample box, orientation and span
 //                    count (whole z-slices, about span_rows rows per span),
@@ -31,8 +36,9 @@
 //                than 2^20 lattice units go to the tet queue, uncertain rows to
 //                the row queue (tets whose rows overflow it are flagged in the
 //                redo bitmap).
-//   k_exact      solves the queued tets and rows with exact integers and ORs
-//                them in (OR is idempotent, so redoing a row is harmless).
+//   k_exact_rows solves the queued rows with exact integers and ORs them in;
+//   k_exact      the queued whole tets and the redo bitmap's (OR is idempotent,
+//                so redoing a row is harmless).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -74,46 +80,63 @@ __global__ void k_prologue(Header *hdr, uint32_t *redo, long long redo_words, ui
 // float as well (a power-of-two scale of a float, overflow aside, which the range check
 // catches), and rintf rounds half to even like the double path: the same X on the FP32
 // pipe instead of GB300's narrow FP64 unit.
-__global__ void k_snap(const float *__restrict__ v, long long n, double ox, double oy, double oz, double h,
-                       double scale, double mul, int use_mul, int fast, int4 *__restrict__ out, Header *hdr) {
+struct SnapArgsK {  // the snap's scalars (see k_snap)
+  double ox, oy, oz, h, scale, mul;
+  int use_mul, fast;
+};
+
+// Vertex i snapped: the lattice point and, in w, its error bits (kErrNan, kErrRange; 0 if
+// valid).  A vertex with w != 0 makes every tet naming it skip.
+__device__ __forceinline__ int4 snap_one(const float *__restrict__ v, long long i, const SnapArgsK &a) {
+  int X[3];
+  int err = 0;
+  const double o[3] = {a.ox, a.oy, a.oz};
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float f = v[3 * i + q];
+    X[q] = 0;
+    if (!isfinite(f)) {
+      err |= kErrNan;
+      continue;
+    }
+    if (a.fast) {
+      const float r = rintf(__fmul_rn(f, (float)a.mul));
+      if (!(fabsf(r) <= (float)kCoordLimit)) {
+        err |= kErrRange;
+        continue;
+      }
+      X[q] = (int)r;
+      continue;
+    }
+    const double d = __dsub_rn((double)f, o[q]);
+    const double x = a.use_mul ? __dmul_rn(d, a.mul) : __dmul_rn(__ddiv_rn(d, a.h), a.scale);
+    const long long r = __double2ll_rn(x);
+    if (r < -kCoordLimit || r > kCoordLimit) {
+      err |= kErrRange;
+      continue;
+    }
+    X[q] = (int)r;
+  }
+  return make_int4(X[0], X[1], X[2], err);
+}
+
+// Lattice vertex i range-checked (w as in snap_one).
+__device__ __forceinline__ int4 load_fixed_one(const int *__restrict__ xyz, long long i) {
+  const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+  const bool bad = x < -kCoordLimit || x > kCoordLimit || y < -kCoordLimit || y > kCoordLimit ||
+                   z < -kCoordLimit || z > kCoordLimit;
+  return make_int4(bad ? 0 : x, bad ? 0 : y, bad ? 0 : z, bad ? kErrRange : 0);
+}
+
+__global__ void k_snap(const float *__restrict__ v, long long n, SnapArgsK a, int4 *__restrict__ out, Header *hdr) {
   chain_wait();  // the prologue has zeroed the header
   chain_release();
   const long long stride = (long long)gridDim.x * blockDim.x;
   int err = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    int X[3];
-    int flag = 0;
-    const double o[3] = {ox, oy, oz};
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      const float f = v[3 * i + q];
-      X[q] = 0;
-      if (!isfinite(f)) {
-        flag = 1;
-        err |= kErrNan;
-        continue;
-      }
-      if (fast) {
-        const float r = rintf(__fmul_rn(f, (float)mul));
-        if (!(fabsf(r) <= (float)kCoordLimit)) {
-          flag = 1;
-          err |= kErrRange;
-          continue;
-        }
-        X[q] = (int)r;
-        continue;
-      }
-      const double d = __dsub_rn((double)f, o[q]);
-      const double x = use_mul ? __dmul_rn(d, mul) : __dmul_rn(__ddiv_rn(d, h), scale);
-      const long long r = __double2ll_rn(x);
-      if (r < -kCoordLimit || r > kCoordLimit) {
-        flag = 1;
-        err |= kErrRange;
-        continue;
-      }
-      X[q] = (int)r;
-    }
-    out[i] = make_int4(X[0], X[1], X[2], flag);
+    const int4 r = snap_one(v, i, a);
+    out[i] = r;
+    err |= r.w;
   }
   if (err) atomicOr(&hdr->status_bits, err);
 }
@@ -124,13 +147,37 @@ __global__ void k_load_fixed(const int *__restrict__ xyz, long long n, int4 *__r
   const long long stride = (long long)gridDim.x * blockDim.x;
   int err = 0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-    const int x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-    const bool bad = x < -kCoordLimit || x > kCoordLimit || y < -kCoordLimit || y > kCoordLimit ||
-                     z < -kCoordLimit || z > kCoordLimit;
-    if (bad) err |= kErrRange;
-    out[i] = make_int4(bad ? 0 : x, bad ? 0 : y, bad ? 0 : z, bad ? 1 : 0);
+    const int4 r = load_fixed_one(xyz, i);
+    out[i] = r;
+    err |= r.w;
   }
   if (err) atomicOr(&hdr->status_bits, err);
+}
+
+// The prologue and the snap (or the lattice load) of a call in one launch, the call's first.
+// The vertices' error bits stay in their w fields; the call's last kernel (k_exact, with
+// p.vflags set) folds them into the status, so nothing here orders against the header's
+// zeroing.
+template <bool FIXED>
+__global__ void k_prep(Header *hdr, uint32_t *redo, long long redo_words, uint32_t *grid, long long n_words,
+                       int clear, const void *__restrict__ src, long long n, SnapArgsK a, int4 *__restrict__ out) {
+  chain_release();  // the next kernel may be scheduled now; it waits for this one to complete
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  if (tid < 64) reinterpret_cast<uint32_t *>(hdr)[tid] = 0u;
+  for (long long i = tid; i < redo_words; i += stride) redo[i] = 0u;
+  if (clear) {
+    if ((reinterpret_cast<uintptr_t>(grid) & 15) == 0) {
+      uint4 *o4 = reinterpret_cast<uint4 *>(grid);
+      const long long n4 = n_words >> 2;
+      for (long long i = tid; i < n4; i += stride) o4[i] = make_uint4(0u, 0u, 0u, 0u);
+      for (long long i = (n4 << 2) + tid; i < n_words; i += stride) grid[i] = 0u;
+    } else {
+      for (long long i = tid; i < n_words; i += stride) grid[i] = 0u;
+    }
+  }
+  for (long long i = tid; i < n; i += stride)
+    out[i] = FIXED ? load_fixed_one(static_cast<const int *>(src), i) : snap_one(static_cast<const float *>(src), i, a);
 }
 
 // Loads, orients (V6 > 0) and boxes a tet already known to be live; returns its extent.
@@ -689,6 +736,14 @@ __global__ void __launch_bounds__(128) k_exact_rows(Params p) {
 template <bool STRICT>
 __global__ void __launch_bounds__(128) k_exact(Params p) {
   chain_wait();  // every tet is queued
+  if (p.vflags) {  // the vertices' error bits, left in verts4[i].w by the fused prologue and snap
+    int err = 0;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < p.n_verts; i += stride)
+      err |= p.verts4[i].w;
+    err = __reduce_or_sync(0xFFFFFFFFu, err);
+    if ((threadIdx.x & 31) == 0 && err) atomicOr(&p.hdr->status_bits, err);
+  }
   exact_tets_job<STRICT>(p);
 }
 
@@ -1081,11 +1136,13 @@ static bool use_slice_units(const voxtet_opts &o, const GridDims &g) {
 
 // Shared tail of both entry points: vertices are already in the workspace.
 static int run_voxelize(const Workspace &w, long long n_verts, const int32_t *tets, long long n_tets,
-                        const GridDims &g, uint32_t *out, const voxtet_opts &o, cudaStream_t stream) {
+                        const GridDims &g, uint32_t *out, const voxtet_opts &o, cudaStream_t stream,
+                        bool vflags = false) {
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   if (n_tets > 0) {
     Params p{};  // every field zero unless set below (list_mode = 0)
+    p.vflags = vflags ? 1 : 0;
     p.verts4 = w.verts4;
     p.tets = reinterpret_cast<const int4 *>(tets);
     p.n_tets = n_tets;
@@ -1224,26 +1281,78 @@ static int common_checks(long long n_verts, const void *tets, long long n_tets, 
   return buffer_checks(n_verts, tets, n_tets, out, ws, ws_bytes);
 }
 
-// Snap kernel launch: X = round_half_even(((double)v - o) / h * 2^(20-K)).
+// The snap's scalars: X = round_half_even(((double)v - o) / h * 2^(20-K)).
+static SnapArgsK snap_args(const float grid_origin[3], float voxel_size, int K) {
+  SnapArgsK a;
+  a.ox = (double)grid_origin[0];
+  a.oy = (double)grid_origin[1];
+  a.oz = (double)grid_origin[2];
+  a.h = (double)voxel_size;
+  a.scale = std::ldexp(1.0, kLatticeBits - K);
+  int e2 = 0;
+  const double mant = std::frexp(a.h, &e2);
+  a.use_mul = mant == 0.5 ? 1 : 0;
+  a.mul = a.use_mul ? std::ldexp(1.0, kLatticeBits - K - (e2 - 1)) : 0.0;
+  a.fast = a.use_mul && a.mul >= 1.0 && a.mul <= 0x1p100 && grid_origin[0] == 0.0f && grid_origin[1] == 0.0f &&
+           grid_origin[2] == 0.0f;
+  return a;
+}
+
+// Snap kernel launch (after a separate prologue; errors go to the header at once).
 static int launch_snap(const Workspace &w, const float *d_verts, long long n_verts, const float grid_origin[3],
                        float voxel_size, int K, cudaStream_t stream) {
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   if (n_verts <= 0) return VOXTET_OK;
-  const double h = (double)voxel_size;
-  const double scale = std::ldexp(1.0, kLatticeBits - K);
-  int e2 = 0;
-  const double mant = std::frexp(h, &e2);
-  const int use_mul = mant == 0.5 ? 1 : 0;
-  const double mul = use_mul ? std::ldexp(1.0, kLatticeBits - K - (e2 - 1)) : 0.0;
-  const int fast = use_mul && mul >= 1.0 && mul <= 0x1p100 && grid_origin[0] == 0.0f && grid_origin[1] == 0.0f &&
-                   grid_origin[2] == 0.0f;
   if (launch_chained(k_snap, (unsigned)grid_blocks(n_verts, 256, dev->sms), 256, 0, stream, d_verts, n_verts,
-                     (double)grid_origin[0], (double)grid_origin[1], (double)grid_origin[2], h, scale, mul, use_mul,
-                     fast, w.verts4, w.hdr) != cudaSuccess)
+                     snap_args(grid_origin, voxel_size, K), w.verts4, w.hdr) != cudaSuccess)
     return VOXTET_ERR_CUDA;
   g_launches.fetch_add(1);
   return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
+}
+
+// The prologue and the vertex snap (FIXED: the lattice load) in one launch.  Only for calls
+// with tets: their k_exact folds the vertices' error bits into the status (p.vflags).
+template <bool FIXED>
+static int launch_prep(const Workspace &w, uint32_t *out, long long n_words, int clear, const void *src,
+                       long long n_verts, const SnapArgsK &a, cudaStream_t stream) {
+  DeviceInfo *dev = nullptr;
+  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+  long long work = n_verts;
+  if (clear && n_words / 4 > work) work = n_words / 4;
+  if (w.redo_words > work) work = w.redo_words;
+  long long blocks = (work + 255) / 256;
+  const long long cap = (long long)dev->sms * 8;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  k_prep<FIXED><<<(unsigned)blocks, 256, 0, stream>>>(w.hdr, w.redo, w.redo_words, out, n_words, clear, src, n_verts,
+                                                      a, w.verts4);
+  g_launches.fetch_add(1);
+  return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
+}
+
+// The front of a dense call: one fused launch when the call has tets (vflags = true: the exact
+// kernel reports the vertices' errors), else the prologue and a snap that reports them itself.
+static int launch_front(const Workspace &w, uint32_t *out, long long n_words, int clear, const void *src,
+                        long long n_verts, long long n_tets, const SnapArgsK &a, bool fixed, cudaStream_t stream,
+                        bool &vflags) {
+  vflags = n_tets > 0 && n_verts > 0;
+  if (vflags)
+    return fixed ? launch_prep<true>(w, out, n_words, clear, src, n_verts, a, stream)
+                 : launch_prep<false>(w, out, n_words, clear, src, n_verts, a, stream);
+  int st = launch_prologue(w, out, n_words, clear, stream);
+  if (st != VOXTET_OK || n_verts <= 0) return st;
+  DeviceInfo *dev = nullptr;
+  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
+  const unsigned blocks = (unsigned)grid_blocks(n_verts, 256, dev->sms);
+  const cudaError_t e =
+      fixed ? launch_chained(k_load_fixed, blocks, 256, 0, stream, static_cast<const int *>(src), n_verts, w.verts4,
+                             w.hdr)
+            : launch_chained(k_snap, blocks, 256, 0, stream, static_cast<const float *>(src), n_verts, a, w.verts4,
+                             w.hdr);
+  if (e != cudaSuccess) return VOXTET_ERR_CUDA;
+  g_launches.fetch_add(1);
+  return VOXTET_OK;
 }
 
 static int float_input_checks(const float *d_verts, long long n_verts, const float grid_origin[3],
@@ -1305,11 +1414,11 @@ int voxelize_tets(const float *d_verts, int64_t n_verts, const int32_t *d_tets, 
   Workspace w;
   workspace_bytes(n_tets, n_verts, &w, d_workspace, ws_bytes);
   const GridDims g = cubic_dims(res, k);
-  st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
+  bool vflags = false;
+  st = launch_front(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, d_verts, n_verts, n_tets,
+                    snap_args(grid_origin, voxel_size, g.K), false, stream, vflags);
   if (st != VOXTET_OK) return st;
-  st = launch_snap(w, d_verts, n_verts, grid_origin, voxel_size, g.K, stream);
-  if (st != VOXTET_OK) return st;
-  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream);
+  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream, vflags);
 }
 
 int voxelize_tets_grid(const float *d_verts, int64_t n_verts, const int32_t *d_tets, int64_t n_tets,
@@ -1332,11 +1441,11 @@ int voxelize_tets_grid(const float *d_verts, int64_t n_verts, const int32_t *d_t
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   Workspace w;
   workspace_bytes(n_tets, n_verts, &w, d_workspace, ws_bytes);
-  st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
+  bool vflags = false;
+  st = launch_front(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, d_verts, n_verts, n_tets,
+                    snap_args(grid_origin, voxel_size, g.K), false, stream, vflags);
   if (st != VOXTET_OK) return st;
-  st = launch_snap(w, d_verts, n_verts, grid_origin, voxel_size, g.K, stream);
-  if (st != VOXTET_OK) return st;
-  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream);
+  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream, vflags);
 }
 
 int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_tets, int64_t n_tets, int32_t res,
@@ -1352,18 +1461,11 @@ int voxelize_tets_fixed(const int32_t *d_xyz, int64_t n_verts, const int32_t *d_
   Workspace w;
   workspace_bytes(n_tets, n_verts, &w, d_workspace, ws_bytes);
   const GridDims g = cubic_dims(res, k);
-  st = launch_prologue(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, stream);
+  bool vflags = false;
+  st = launch_front(w, d_out_bits, g.out_words(), o.accumulate ? 0 : 1, d_xyz, n_verts, n_tets, SnapArgsK{}, true,
+                    stream, vflags);
   if (st != VOXTET_OK) return st;
-  DeviceInfo *dev = nullptr;
-  if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
-  if (n_verts > 0) {
-    if (launch_chained(k_load_fixed, (unsigned)grid_blocks(n_verts, 256, dev->sms), 256, 0, stream, d_xyz, n_verts,
-                       w.verts4, w.hdr) != cudaSuccess)
-      return VOXTET_ERR_CUDA;
-    g_launches.fetch_add(1);
-    if (cudaGetLastError() != cudaSuccess) return VOXTET_ERR_CUDA;
-  }
-  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream);
+  return run_voxelize(w, n_verts, d_tets, n_tets, g, d_out_bits, o, stream, vflags);
 }
 
 int voxtet_last_status(const void *d_workspace, void *stream_) {

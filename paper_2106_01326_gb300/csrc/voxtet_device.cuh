@@ -79,7 +79,7 @@ struct Params {
   long long big_tiles;  // single-mesh launch: tiles of kTile tets before the kSmallTile tail
   long long tile_stride;  // > 0: tile k holds tets k + j * tile_stride (slab launches), else contiguous tiles
   int list_mode;    // span kernel: 1 = its tets are the hdr->listq_count ones listed at the back of tetq
-  int pad1;
+  int vflags;       // exact kernel: 1 = fold the vertices' error bits (verts4[i].w) into the status
 };
 
 // Row-queue capacity for a mesh of n_tets tets.

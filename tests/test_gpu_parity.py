@@ -264,6 +264,19 @@ def test_error_statuses(vt):
     xyz = np.array([[0, 0, 0], [(1 << 21) + 1, 0, 0], [0, L, 0], [0, 0, L]], dtype=np.int32)
     st, _ = vt.voxelize_fixed(dt(xyz), dt(t), 8, raise_on_error=False)
     assert st == vt.ERR_RANGE
+    # a bad vertex no tet names is reported too: with tets (the snap's error bits are folded in
+    # by the last kernel of the call) and without any (the snap reports them itself)
+    extra = np.concatenate([v, np.array([[np.nan, 0.5, 0.5]], np.float32)])
+    st, _ = vt.voxelize(dv(extra), dt(t), (0, 0, 0), 0.25, 4, raise_on_error=False)
+    assert st == vt.ERR_NAN
+    st, _ = vt.voxelize(dv(extra), dt(np.zeros((0, 4), np.int32)), (0, 0, 0), 0.25, 4, raise_on_error=False)
+    assert st == vt.ERR_NAN
+    st, _ = vt.voxelize_grid(dv(extra), dt(t), (0, 0, 0), 0.25, (4, 3, 2), raise_on_error=False)
+    assert st == vt.ERR_NAN
+    xyz_extra = np.concatenate([xyz[:1], np.array([[0, L, 0], [L, 0, 0], [0, 0, L], [-(1 << 21) - 5, 0, 0]],
+                                                  np.int32)])
+    st, _ = vt.voxelize_fixed(dt(xyz_extra), dt(t), 8, raise_on_error=False)
+    assert st == vt.ERR_RANGE
     # asynchronous form: the status is read afterwards from the workspace
     ws = vt.alloc_workspace(1, 4, 4)
     st, _ = vt.voxelize(dv(bad), dt(t), (0, 0, 0), 0.25, 4, workspace=ws, sync=False, raise_on_error=False)
