@@ -50,21 +50,34 @@ class JobSpec:
             self.voxel_size = 1.0 / self.res
 
 
+_JOB_DTYPE = None
+
+
+def _job_dtype():
+    """numpy view of ``voxtet.Job`` (the C voxtet_job), field for field at its offsets."""
+    global _JOB_DTYPE
+    if _JOB_DTYPE is None:
+        import numpy as np
+
+        formats = {"d_verts": np.uint64, "n_verts": np.int64, "d_tets": np.uint64, "n_tets": np.int64,
+                   "origin": (np.float32, 3), "voxel_size": np.float32, "res": np.int32, "span_rows": np.int32,
+                   "fixed_point": np.int32, "reserved": np.int32, "d_out_bits": np.uint64}
+        names = [f[0] for f in vt.Job._fields_]
+        _JOB_DTYPE = np.dtype({"names": names, "formats": [formats[n] for n in names],
+                               "offsets": [getattr(vt.Job, n).offset for n in names],
+                               "itemsize": ctypes.sizeof(vt.Job)})
+    return _JOB_DTYPE
+
+
 def make_jobs(specs: Sequence[JobSpec]):
-    arr = (vt.Job * max(len(specs), 1))()
-    for i, sp in enumerate(specs):
-        j = arr[i]
-        j.d_verts = sp.mesh.verts.data_ptr()
-        j.n_verts = sp.mesh.n_verts
-        j.d_tets = sp.mesh.tets.data_ptr()
-        j.n_tets = sp.mesh.n_tets
-        j.origin[0], j.origin[1], j.origin[2] = (float(x) for x in sp.origin)
-        j.voxel_size = float(sp.voxel_size)
-        j.res = int(sp.res)
-        j.span_rows = int(sp.span_rows)
-        j.fixed_point = 0
-        j.d_out_bits = sp.out.data_ptr()
-    return arr
+    """The job table of a batch (a ctypes ``voxtet.Job`` array), built in one numpy pass: a
+    plan rebuilds it every run, so its cost is part of each batch's latency."""
+    import numpy as np
+
+    rows = [(sp.mesh.verts.data_ptr(), sp.mesh.verts.shape[0], sp.mesh.tets.data_ptr(), sp.mesh.tets.shape[0],
+             sp.origin, sp.voxel_size, sp.res, sp.span_rows, 0, 0, sp.out.data_ptr()) for sp in specs]
+    a = np.array(rows, dtype=_job_dtype()) if rows else np.zeros(1, dtype=_job_dtype())
+    return (vt.Job * len(a)).from_buffer(a)  # shares a's memory and keeps it alive
 
 
 def batch_workspace_size(specs: Sequence[JobSpec], max_jobs: Optional[int] = None) -> int:

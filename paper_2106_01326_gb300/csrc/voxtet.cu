@@ -686,11 +686,11 @@ __device__ __forceinline__ void exact_tet(const Params &p, long long t) {
   else exact_tet_rows<STRICT, i128>(p, V, bx);
 }
 
-// The queued rows of one mesh (a thread each).
+// The queued rows of one mesh (a thread each), by blocks bi of bn.
 template <bool STRICT>
-__device__ __forceinline__ void exact_rows_job(const Params &p) {
+__device__ __forceinline__ void exact_rows_job(const Params &p, unsigned bi, unsigned bn) {
   const unsigned n_rq = min(p.hdr->rowq_count, p.q_cap);
-  const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x, gsz = gridDim.x * blockDim.x;
+  const unsigned gtid = bi * blockDim.x + threadIdx.x, gsz = bn * blockDim.x;
   for (unsigned i = gtid; i < n_rq; i += gsz) {
     const RowItem it = p.rowq[i];
     int3 V[4];
@@ -707,21 +707,21 @@ __device__ __forceinline__ void exact_rows_job(const Params &p) {
 }
 
 // The rest of the exact work of one mesh: its queued tets (a block each) and, after a
-// row-queue overflow, the tets flagged in its redo bitmap.
+// row-queue overflow, the tets flagged in its redo bitmap; by blocks bi of bn.
 template <bool STRICT>
-__device__ __forceinline__ void exact_tets_job(const Params &p) {
+__device__ __forceinline__ void exact_tets_job(const Params &p, unsigned bi, unsigned bn) {
   const unsigned n_tq = min((unsigned long long)p.hdr->tetq_count, (unsigned long long)p.n_tets);
-  for (unsigned q = blockIdx.x; q < n_tq; q += gridDim.x) exact_tet<STRICT>(p, p.tetq[q]);
+  for (unsigned q = bi; q < n_tq; q += bn) exact_tet<STRICT>(p, p.tetq[q]);
   if (p.hdr->rowq_count > p.q_cap) {
-    for (long long t = blockIdx.x; t < p.n_tets; t += gridDim.x)
+    for (long long t = bi; t < p.n_tets; t += bn)
       if ((p.redo[t >> 5] >> (t & 31)) & 1u) exact_tet<STRICT>(p, t);
   }
 }
 
 template <bool STRICT>
-__device__ __forceinline__ void exact_job(const Params &p) {
-  exact_tets_job<STRICT>(p);
-  exact_rows_job<STRICT>(p);
+__device__ __forceinline__ void exact_job(const Params &p, unsigned bi, unsigned bn) {
+  exact_tets_job<STRICT>(p, bi, bn);
+  exact_rows_job<STRICT>(p, bi, bn);
 }
 
 // The queued rows, in a kernel of their own: the 64-bit row solve needs far fewer registers
@@ -730,7 +730,7 @@ template <bool STRICT>
 __global__ void __launch_bounds__(128) k_exact_rows(Params p) {
   chain_wait();  // every row is queued
   chain_release();
-  exact_rows_job<STRICT>(p);
+  exact_rows_job<STRICT>(p, blockIdx.x, gridDim.x);
 }
 
 template <bool STRICT>
@@ -744,7 +744,7 @@ __global__ void __launch_bounds__(128) k_exact(Params p) {
     err = __reduce_or_sync(0xFFFFFFFFu, err);
     if ((threadIdx.x & 31) == 0 && err) atomicOr(&p.hdr->status_bits, err);
   }
-  exact_tets_job<STRICT>(p);
+  exact_tets_job<STRICT>(p, blockIdx.x, gridDim.x);
 }
 
 // ------------------------------------------------------------------ batched kernels
@@ -796,26 +796,26 @@ __device__ __forceinline__ int find_job(const unsigned long long *base, int n, u
   return a;
 }
 
-__global__ void k_prologue_batched(const BatchHeader *bh, const JobDesc *jobs) {
+// Every job's header (64 words), redo bitmap and, unless accumulating, grid, zeroed in one
+// pass: word g of the batch's zeroing belongs to the job j with zero_base[j] <= g <
+// zero_base[j + 1] (host-built prefix), so consecutive threads store consecutive words
+// whatever the jobs' sizes, instead of every thread visiting every job in turn.
+__global__ void k_prologue_batched(const BatchHeader *bh, const JobDesc *jobs, const unsigned long long *zero_base) {
   const int n = bh->n_jobs;
-  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (int j = 0; j < n; ++j) {
+  if (n <= 0) return;
+  const unsigned long long total = zero_base[n];
+  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+  unsigned long long g = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= total) return;
+  int j = find_job(zero_base, n, g);
+  for (; g < total; g += stride) {
+    while (g >= zero_base[j + 1]) ++j;  // zero_base[n] = total > g, so j stays below n
     const Params &p = jobs[j].p;
-    if (tid < 64) reinterpret_cast<uint32_t *>(p.hdr)[tid] = 0u;
+    const long long i = (long long)(g - zero_base[j]);
     const long long redo_words = (p.n_tets + 31) / 32;
-    for (long long i = tid; i < redo_words; i += stride) p.redo[i] = 0u;
-    if (jobs[j].z.clear) {
-      uint32_t *out = p.out;
-      const long long nw = jobs[j].z.grid_words;
-      if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {
-        uint4 *o4 = reinterpret_cast<uint4 *>(out);
-        for (long long i = tid; i < (nw >> 2); i += stride) o4[i] = make_uint4(0u, 0u, 0u, 0u);
-        for (long long i = ((nw >> 2) << 2) + tid; i < nw; i += stride) out[i] = 0u;
-      } else {
-        for (long long i = tid; i < nw; i += stride) out[i] = 0u;
-      }
-    }
+    if (i < 64) reinterpret_cast<uint32_t *>(p.hdr)[i] = 0u;
+    else if (i < 64 + redo_words) p.redo[i - 64] = 0u;
+    else p.out[i - 64 - redo_words] = 0u;  // counted only when the job clears its grid
   }
 }
 
@@ -914,10 +914,18 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
   if (cur >= 0) flush_counters(sp.hdr, ctr);
 }
 
+// The exact work of every job at once: job j owns blocks block_base[j] .. block_base[j + 1] - 1
+// (a host-built share of the grid, at least one block, more for jobs with more tets), so no
+// block visits the jobs one after another.
 template <bool STRICT>
-__global__ void __launch_bounds__(128) k_exact_batched(const BatchHeader *bh, const JobDesc *jobs) {
+__global__ void __launch_bounds__(128) k_exact_batched(const BatchHeader *bh, const JobDesc *jobs,
+                                                       const unsigned long long *block_base) {
   const int n = bh->n_jobs;
-  for (int j = 0; j < n; ++j) exact_job<STRICT>(jobs[j].p);
+  if (n <= 0 || blockIdx.x >= block_base[n]) return;
+  const int j = find_job(block_base, n, blockIdx.x);
+  const unsigned bi = blockIdx.x - (unsigned)block_base[j];
+  const unsigned bn = (unsigned)(block_base[j + 1] - block_base[j]);
+  exact_job<STRICT>(jobs[j].p, bi, bn);
 }
 
 // Copies each job's device-detected error bits into a dense array for one readback.
@@ -1534,11 +1542,11 @@ uint64_t voxtet_launch_count(void) { return g_launches.load(); }
 namespace voxtet {
 
 // Layout of a batch workspace: BatchHeader, JobDesc[cap], tile_base[cap + 1],
-// vert_base[cap + 1], status[cap] (each 256-byte aligned), then one single-mesh
-// workspace slice per job.  The leading part (up to the first slice) is built on
-// the host and uploaded with one copy per run.
+// vert_base[cap + 1], zero_base[cap + 1], block_base[cap + 1], status[cap] (each 256-byte
+// aligned), then one single-mesh workspace slice per job.  The leading part (up to the
+// first slice) is built on the host and uploaded with one copy per run.
 struct BatchLayout {
-  size_t o_table, o_tiles, o_verts, o_status, o_slices;
+  size_t o_table, o_tiles, o_verts, o_zero, o_blocks, o_status, o_slices;
 };
 
 static BatchLayout batch_layout(int cap) {
@@ -1549,6 +1557,10 @@ static BatchLayout batch_layout(int cap) {
   L.o_tiles = o;
   o += align256((size_t)(cap + 1) * sizeof(unsigned long long));
   L.o_verts = o;
+  o += align256((size_t)(cap + 1) * sizeof(unsigned long long));
+  L.o_zero = o;
+  o += align256((size_t)(cap + 1) * sizeof(unsigned long long));
+  L.o_blocks = o;
   o += align256((size_t)(cap + 1) * sizeof(unsigned long long));
   L.o_status = o;
   o += align256((size_t)cap * sizeof(int));
@@ -1576,6 +1588,14 @@ static size_t job_slice_bytes(const voxtet_job &j, bool valid) {
   return valid ? align256(voxtet_workspace_size(j.n_tets, j.n_verts, j.res)) : align256(sizeof(Header));
 }
 
+// Blocks of the batched exact kernel: fixed per capacity (a plan's graph keeps its launch
+// shape while its jobs change), at least one per job.
+static long long exact_batch_blocks(int cap) {
+  DeviceInfo *dev = nullptr;
+  const long long sms = device_info(dev) == cudaSuccess ? dev->sms : 152;
+  return cap > sms * 4 ? (long long)cap : sms * 4;
+}
+
 // Builds the host image of the table part of a batch workspace.  Returns the bytes
 // of workspace the batch needs (0 on a batch-level argument error).
 static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const voxtet_opts &o, char *ws_dev,
@@ -1597,8 +1617,14 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
   JobDesc *tab = reinterpret_cast<JobDesc *>(img + L.o_table);
   unsigned long long *tiles = reinterpret_cast<unsigned long long *>(img + L.o_tiles);
   unsigned long long *vbase = reinterpret_cast<unsigned long long *>(img + L.o_verts);
+  unsigned long long *zbase = reinterpret_cast<unsigned long long *>(img + L.o_zero);
+  unsigned long long *bbase = reinterpret_cast<unsigned long long *>(img + L.o_blocks);
   size_t off = L.o_slices;
-  unsigned long long tsum = 0, vsum = 0;
+  unsigned long long tsum = 0, vsum = 0, zsum = 0;
+  long long all_tets = 0;
+  for (int j = 0; j < n; ++j) all_tets += ok[j] ? jobs[j].n_tets : 0;
+  const long long spare = exact_batch_blocks(cap) - n;  // blocks beyond one per job, shared by tets
+  unsigned long long bsum = 0;
   for (int j = 0; j < n; ++j) {
     const voxtet_job &J = jobs[j];
     const long long nt = ok[j] ? J.n_tets : 0, nv = ok[j] ? J.n_verts : 0;
@@ -1648,11 +1674,18 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
     d.z.clear = (ok[j] && !o.accumulate) ? 1 : 0;
     tiles[j] = tsum;
     vbase[j] = vsum;
+    zbase[j] = zsum;
+    bbase[j] = bsum;
     tsum += (unsigned long long)((nt + kTile - 1) / kTile);
     vsum += (unsigned long long)nv;
+    // header words, redo bitmap words, grid words (k_prologue_batched's order)
+    zsum += 64ull + (unsigned long long)((nt + 31) / 32) + (d.z.clear ? (unsigned long long)d.z.grid_words : 0ull);
+    bsum += 1ull + (all_tets > 0 && spare > 0 ? (unsigned long long)((double)spare * (double)nt / (double)all_tets) : 0ull);
   }
   tiles[n] = tsum;
   vbase[n] = vsum;
+  zbase[n] = zsum;
+  bbase[n] = bsum;
   bh->n_jobs = n;
   bh->total_tiles = tsum;
   bh->total_verts = vsum;
@@ -1669,21 +1702,24 @@ static int launch_batch(char *ws, int cap, int strict, cudaStream_t stream) {
   JobDesc *tab = reinterpret_cast<JobDesc *>(ws + L.o_table);
   const unsigned long long *tiles = reinterpret_cast<const unsigned long long *>(ws + L.o_tiles);
   const unsigned long long *vbase = reinterpret_cast<const unsigned long long *>(ws + L.o_verts);
+  const unsigned long long *zbase = reinterpret_cast<const unsigned long long *>(ws + L.o_zero);
+  const unsigned long long *bbase = reinterpret_cast<const unsigned long long *>(ws + L.o_blocks);
   int *status = reinterpret_cast<int *>(ws + L.o_status);
   const unsigned g8 = (unsigned)dev->sms * 8;
-  k_prologue_batched<<<g8, 256, 0, stream>>>(bh, tab);
+  const unsigned eb = (unsigned)exact_batch_blocks(cap);
+  k_prologue_batched<<<g8, 256, 0, stream>>>(bh, tab, zbase);
   k_snap_batched<<<g8, 256, 0, stream>>>(bh, tab, vbase);
   int occ = 0;
   if (strict) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<true>, kBlock, slice_table_bytes(16));
     k_voxelize_batched<true><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, slice_table_bytes(16), stream>>>(
         bh, tab, tiles);
-    k_exact_batched<true><<<(unsigned)dev->sms * 4, kExactBlock, 0, stream>>>(bh, tab);
+    k_exact_batched<true><<<eb, kExactBlock, 0, stream>>>(bh, tab, bbase);
   } else {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<false>, kBlock, slice_table_bytes(16));
     k_voxelize_batched<false><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, slice_table_bytes(16), stream>>>(
         bh, tab, tiles);
-    k_exact_batched<false><<<(unsigned)dev->sms * 4, kExactBlock, 0, stream>>>(bh, tab);
+    k_exact_batched<false><<<eb, kExactBlock, 0, stream>>>(bh, tab, bbase);
   }
   k_gather_status<<<(cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, 256, 0, stream>>>(bh, tab, status);
   g_launches.fetch_add(5);
