@@ -877,7 +877,13 @@ __global__ void k_snap_batched(const BatchHeader *bh, const JobDesc *jobs, const
   }
 }
 
-template <bool STRICT>
+// Row culling of a batch's jobs: none of them, all of them, or per job.  A batch of one kind
+// runs a kernel with only that tile path compiled in (the kernel holding both spills: 328 B
+// per thread at 80 registers against 92 B; measured on GB300, 256 jobs at 32^3-128^3: a
+// replay 1.00 -> 0.94 ms).
+enum BatchCull { kCullNone = 0, kCullAll = 1, kCullPerJob = 2 };
+
+template <bool STRICT, int CM>
 __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
     k_voxelize_batched(BatchHeader *bh, const JobDesc *jobs, const unsigned long long *tile_base) {
   __shared__ TileSmem sm;
@@ -908,8 +914,10 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
     }
     const long long base = (long long)(tile_s - tile_base[j]) * kTile;
     const long long end = min(sp.n_tets, base + kTile);
-    if (sp.cull) process_tile<STRICT, true, false, false>(sp, base, end, sm, slice_tab, ctr);
-    else process_tile<STRICT, false, false, false>(sp, base, end, sm, slice_tab, ctr);
+    if (CM == kCullAll || (CM == kCullPerJob && sp.cull))
+      process_tile<STRICT, CM != kCullNone, false, false>(sp, base, end, sm, slice_tab, ctr);
+    else
+      process_tile<STRICT, false, false, false>(sp, base, end, sm, slice_tab, ctr);
   }
   if (cur >= 0) flush_counters(sp.hdr, ctr);
 }
@@ -1599,7 +1607,7 @@ static long long exact_batch_blocks(int cap) {
 // Builds the host image of the table part of a batch workspace.  Returns the bytes
 // of workspace the batch needs (0 on a batch-level argument error).
 static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const voxtet_opts &o, char *ws_dev,
-                                std::vector<char> *image, int *host_status) {
+                                std::vector<char> *image, int *host_status, int *cull_kind = nullptr) {
   const BatchLayout L = batch_layout(cap);
   size_t need = L.o_slices;
   std::vector<int> ok(n);
@@ -1686,6 +1694,15 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
   vbase[n] = vsum;
   zbase[n] = zsum;
   bbase[n] = bsum;
+  if (cull_kind) {  // which tile paths the jobs with tets need
+    int with = 0, without = 0;
+    for (int j = 0; j < n; ++j) {
+      if (!ok[j] || jobs[j].n_tets == 0) continue;
+      if (tab[j].p.cull) ++with;
+      else ++without;
+    }
+    *cull_kind = with && without ? kCullPerJob : (with ? kCullAll : kCullNone);
+  }
   bh->n_jobs = n;
   bh->total_tiles = tsum;
   bh->total_verts = vsum;
@@ -1693,8 +1710,19 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
   return need;
 }
 
-// Enqueues the batch kernels on `stream` (the table must already be uploaded).
-static int launch_batch(char *ws, int cap, int strict, cudaStream_t stream) {
+typedef void (*BatchVoxKernel)(BatchHeader *, const JobDesc *, const unsigned long long *);
+
+static BatchVoxKernel batch_vox_kernel(bool strict, int cull) {
+  if (strict)
+    return cull == kCullNone ? k_voxelize_batched<true, kCullNone>
+                             : (cull == kCullAll ? k_voxelize_batched<true, kCullAll> : k_voxelize_batched<true, kCullPerJob>);
+  return cull == kCullNone ? k_voxelize_batched<false, kCullNone>
+                           : (cull == kCullAll ? k_voxelize_batched<false, kCullAll> : k_voxelize_batched<false, kCullPerJob>);
+}
+
+// Enqueues the batch kernels on `stream` (the table must already be uploaded); `cull` is the
+// batch's BatchCull kind (build_batch_image).
+static int launch_batch(char *ws, int cap, int strict, int cull, cudaStream_t stream) {
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   const BatchLayout L = batch_layout(cap);
@@ -1710,17 +1738,11 @@ static int launch_batch(char *ws, int cap, int strict, cudaStream_t stream) {
   k_prologue_batched<<<g8, 256, 0, stream>>>(bh, tab, zbase);
   k_snap_batched<<<g8, 256, 0, stream>>>(bh, tab, vbase);
   int occ = 0;
-  if (strict) {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<true>, kBlock, slice_table_bytes(16));
-    k_voxelize_batched<true><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, slice_table_bytes(16), stream>>>(
-        bh, tab, tiles);
-    k_exact_batched<true><<<eb, kExactBlock, 0, stream>>>(bh, tab, bbase);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_voxelize_batched<false>, kBlock, slice_table_bytes(16));
-    k_voxelize_batched<false><<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, slice_table_bytes(16), stream>>>(
-        bh, tab, tiles);
-    k_exact_batched<false><<<eb, kExactBlock, 0, stream>>>(bh, tab, bbase);
-  }
+  const BatchVoxKernel vk = batch_vox_kernel(strict != 0, cull);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, vk, kBlock, slice_table_bytes(16));
+  vk<<<(unsigned)dev->sms * (occ > 0 ? occ : 1), kBlock, slice_table_bytes(16), stream>>>(bh, tab, tiles);
+  if (strict) k_exact_batched<true><<<eb, kExactBlock, 0, stream>>>(bh, tab, bbase);
+  else k_exact_batched<false><<<eb, kExactBlock, 0, stream>>>(bh, tab, bbase);
   k_gather_status<<<(cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1, 256, 0, stream>>>(bh, tab, status);
   g_launches.fetch_add(5);
   return cudaGetLastError() == cudaSuccess ? VOXTET_OK : VOXTET_ERR_CUDA;
@@ -1749,7 +1771,7 @@ struct voxtet_plan {
   char *pinned = nullptr;  // host image of the table part, uploaded by the graph
   size_t image_bytes = 0;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};  // one graph per BatchCull kind, captured on first use
   cudaEvent_t done = nullptr;
   bool in_flight = false;
   int n_jobs = 0;
@@ -1777,12 +1799,14 @@ int voxelize_tets_batched(const voxtet_job *jobs, int32_t n_jobs, void *d_ws, si
   const int cap = n_jobs > 0 ? n_jobs : 1;
   std::vector<int> hs((size_t)cap, VOXTET_OK);
   std::vector<char> image;
-  const size_t need = build_batch_image(jobs, n_jobs, cap, o, reinterpret_cast<char *>(d_ws), &image, hs.data());
+  int cull = kCullPerJob;
+  const size_t need =
+      build_batch_image(jobs, n_jobs, cap, o, reinterpret_cast<char *>(d_ws), &image, hs.data(), &cull);
   if (need > ws_bytes) return VOXTET_ERR_WORKSPACE;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (cudaMemcpyAsync(d_ws, image.data(), image.size(), cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return VOXTET_ERR_CUDA;
-  st = launch_batch(reinterpret_cast<char *>(d_ws), cap, o.mode == 1, stream);
+  st = launch_batch(reinterpret_cast<char *>(d_ws), cap, o.mode == 1, cull, stream);
   if (st != VOXTET_OK) return st;
   if (o.sync) {
     st = read_job_status(reinterpret_cast<char *>(d_ws), cap, n_jobs, hs.data(), stream);
@@ -1826,29 +1850,31 @@ int voxtet_plan_run(voxtet_plan *p, const voxtet_job *jobs, int32_t n_jobs, void
   p->in_flight = false;
   p->host_status.assign((size_t)(n_jobs > 0 ? n_jobs : 1), VOXTET_OK);
   std::vector<char> image;
-  const size_t need = build_batch_image(jobs, n_jobs, p->cap, p->opts, p->ws, &image, p->host_status.data());
+  int cull = kCullPerJob;
+  const size_t need = build_batch_image(jobs, n_jobs, p->cap, p->opts, p->ws, &image, p->host_status.data(), &cull);
   if (need > p->ws_bytes) return VOXTET_ERR_NOMEM;
   std::memcpy(p->pinned, image.data(), p->image_bytes);
-  if (!p->exec) {  // capture the upload and the kernels once; later runs replay them
+  cudaGraphExec_t &exec = p->exec[cull];
+  if (!exec) {  // capture the upload and the kernels once per kind; later runs replay them
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VOXTET_ERR_CUDA;
     cudaMemcpyAsync(p->ws, p->pinned, p->image_bytes, cudaMemcpyHostToDevice, p->cap_stream);
     const unsigned long long before = g_launches.load();
-    const int st = launch_batch(p->ws, p->cap, p->opts.mode == 1, p->cap_stream);
+    const int st = launch_batch(p->ws, p->cap, p->opts.mode == 1, cull, p->cap_stream);
     g_launches.store(before);  // captured, not launched
     if (cudaStreamEndCapture(p->cap_stream, &g) != cudaSuccess || st != VOXTET_OK) {
       if (g) cudaGraphDestroy(g);
       return VOXTET_ERR_CUDA;
     }
-    const cudaError_t e = cudaGraphInstantiate(&p->exec, g, 0);
+    const cudaError_t e = cudaGraphInstantiate(&exec, g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-      p->exec = nullptr;
+      exec = nullptr;
       return VOXTET_ERR_CUDA;
     }
   }
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
-  if (cudaGraphLaunch(p->exec, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
+  if (cudaGraphLaunch(exec, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
   g_launches.fetch_add(5);
   if (cudaEventRecord(p->done, stream) != cudaSuccess) return VOXTET_ERR_CUDA;
   p->in_flight = true;
@@ -1879,7 +1905,8 @@ int voxtet_plan_query(voxtet_plan *p) {
 void voxtet_plan_destroy(voxtet_plan *p) {
   if (!p) return;
   if (p->in_flight && p->done) cudaEventSynchronize(p->done);
-  if (p->exec) cudaGraphExecDestroy(p->exec);
+  for (cudaGraphExec_t &e : p->exec)
+    if (e) cudaGraphExecDestroy(e);
   if (p->done) cudaEventDestroy(p->done);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->pinned) cudaFreeHost(p->pinned);

@@ -79,6 +79,30 @@ def test_plan_replays_with_different_batches(env, workload, mode):
         plan.close()
 
 
+def test_plan_batches_of_each_culling_kind(env, workload):
+    """A batch whose jobs all skip rows outside the cross-sections (grids from 256 per side),
+    one whose jobs never do, and a mix: each kind runs its own compiled tile path and the plan
+    keeps a graph per kind; every grid equals the job's single call, in any order of runs."""
+    vt, batch = env
+    small = [j for j in workload if j.res < 256][:10]
+    large = [j for j in workload if j.res >= 256][:4]
+    assert small and large
+    kinds = [_specs(batch, vt, small), _specs(batch, vt, large), _specs(batch, vt, small[:5] + large[:2])]
+    need = max(batch.batch_workspace_size(s, 16) for s in kinds)
+    plan = batch.Plan(need, 16)
+    try:
+        for specs in (kinds[0], kinds[1], kinds[2], kinds[0], kinds[2]):
+            for sp in specs:
+                sp.out.fill_(-1)
+            assert plan.run(specs) == vt.OK
+            assert plan.wait() == [vt.OK] * len(specs)
+            for sp in specs:
+                ref = vt.voxelize(sp.mesh.verts, sp.mesh.tets, sp.origin, sp.voxel_size, sp.res)
+                assert bool((sp.out == ref).all()), sp.res
+    finally:
+        plan.close()
+
+
 def test_plan_reports_workspace_overflow(env, workload):
     vt, batch = env
     specs = _specs(batch, vt, workload[:8])
