@@ -87,9 +87,10 @@ typedef struct {
                            longest side is in [1024, 2048), 64 for the slabs of voxelize_tets_sparse) */
     int32_t block;      /* threads per block of the scanline kernel; 0 = automatic (only 128 is accepted) */
     int32_t profile;    /* 1 = record CUDA events around the main kernel on `stream` (see voxtet_stats) */
-    int32_t row_cull;   /* skip x-rows outside each z-slice's cross-section: 0 = automatic, 1 = on, 2 = off */
+    int32_t row_cull;   /* skip x-rows outside each z-slice's cross-section: 0 = automatic (on: it measured
+                           faster at every grid size), 1 = on, 2 = off */
     int32_t kernel;     /* work distribution of the scanline step: 0 = automatic (slice units when the grid's
-                           longest side is in [256, 1024], else spans), 1 = spans (runs of whole z-slices of
+                           longest side is at most 1024, else spans), 1 = spans (runs of whole z-slices of
                            one tet per thread, sorted by estimated work), 2 = slice units (one (tet, z-slice)
                            per thread, sorted by exact row count; tets spanning more than 32 slices or 1024
                            rows per slice still go to spans).  Same grid either way; batches use spans. */

@@ -68,7 +68,8 @@ class Arena:
         return self.buf[off:off + n].view(dtype=__import__("torch").int32).view(res, res, w)
 
 
-CULL_MIN_RES = 256  # grid side from which a job skips rows outside each z-slice's cross-section
+CULL_MIN_RES = 1  # grid side from which a job skips rows outside each z-slice's cross-section (the
+                  # library's automatic choice: every grid)
 
 
 def grid_bytes(res: int) -> int:
@@ -216,6 +217,7 @@ class Server:
                 # a batch of one culling kind (grids from CULL_MIN_RES per side skip rows outside
                 # each cross-section, smaller ones do not): such a batch runs the kernel with only
                 # that tile path compiled in; requests of the other kind keep their queue order
+                # (with the automatic choice every request is of one kind)
                 specs, group, used = [], [], self.table_bytes
                 kind = admitted[0].res >= CULL_MIN_RES
                 rest = deque()
