@@ -86,7 +86,7 @@ def batch_workspace_size(specs: Sequence[JobSpec], max_jobs: Optional[int] = Non
 
 
 def voxelize_batched(specs: Sequence[JobSpec], workspace=None, mode: int = 0, use_filter: bool = True,
-                     sync: bool = True, stream=None) -> List[int]:
+                     sync: bool = True, stream=None, row_cull: int = 0) -> List[int]:
     """One batched call (no graph).  Returns the per-job status codes."""
     import torch
 
@@ -96,7 +96,7 @@ def voxelize_batched(specs: Sequence[JobSpec], workspace=None, mode: int = 0, us
     if workspace is None:
         workspace = torch.empty(batch_workspace_size(specs), dtype=torch.uint8, device="cuda")
     st_arr = (ctypes.c_int32 * max(n, 1))()
-    o = vt.make_opts(mode, False, use_filter, sync)
+    o = vt.make_opts(mode, False, use_filter, sync, row_cull=row_cull)
     st = lib.voxelize_tets_batched(jobs, n, workspace.data_ptr(), workspace.numel(), ctypes.byref(o),
                                    vt._stream_ptr(stream), st_arr)
     if st != vt.OK:
@@ -111,14 +111,14 @@ class Plan:
     """
 
     def __init__(self, workspace_bytes: int, max_jobs: int, mode: int = 0, use_filter: bool = True,
-                 device=None):
+                 device=None, row_cull: int = 0):
         import torch
 
         self.lib = vt.load()
         self.workspace = torch.empty(int(workspace_bytes), dtype=torch.uint8, device=device or "cuda")
         self.max_jobs = int(max_jobs)
         self._handle = ctypes.c_void_p()
-        o = vt.make_opts(mode, False, use_filter, sync=False)
+        o = vt.make_opts(mode, False, use_filter, sync=False, row_cull=row_cull)
         st = self.lib.voxtet_plan_create(self.workspace.data_ptr(), self.workspace.numel(), self.max_jobs,
                                          ctypes.byref(o), ctypes.byref(self._handle))
         if st != vt.OK:

@@ -877,13 +877,13 @@ __global__ void k_snap_batched(const BatchHeader *bh, const JobDesc *jobs, const
   }
 }
 
-// Row culling of a batch's jobs: none of them, all of them, or per job.  A batch of one kind
-// runs a kernel with only that tile path compiled in (the kernel holding both spills: 328 B
-// per thread at 80 registers against 92 B; measured on GB300, 256 jobs at 32^3-128^3: a
-// replay 1.00 -> 0.94 ms).
-enum BatchCull { kCullNone = 0, kCullAll = 1, kCullPerJob = 2 };
+// Row culling is one choice for a whole batch (opts->row_cull; the automatic choice culls at
+// every grid side), so the kernel is compiled per choice with only that tile path in it (the
+// kernel holding both spilled 328 B per thread at 80 registers against 92 B; measured on
+// GB300, 256 jobs at 32^3-128^3: a replay 1.00 -> 0.94 ms).
+static_assert(kCullMinRes <= 1, "the jobs of a batch share one culling choice");
 
-template <bool STRICT, int CM>
+template <bool STRICT, bool CULL>
 __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
     k_voxelize_batched(BatchHeader *bh, const JobDesc *jobs, const unsigned long long *tile_base) {
   __shared__ TileSmem sm;
@@ -914,10 +914,7 @@ __global__ void __launch_bounds__(kBlock, VOXTET_MIN_BLOCKS)
     }
     const long long base = (long long)(tile_s - tile_base[j]) * kTile;
     const long long end = min(sp.n_tets, base + kTile);
-    if (CM == kCullAll || (CM == kCullPerJob && sp.cull))
-      process_tile<STRICT, CM != kCullNone, false, false>(sp, base, end, sm, slice_tab, ctr);
-    else
-      process_tile<STRICT, false, false, false>(sp, base, end, sm, slice_tab, ctr);
+    process_tile<STRICT, CULL, false, false>(sp, base, end, sm, slice_tab, ctr);
   }
   if (cur >= 0) flush_counters(sp.hdr, ctr);
 }
@@ -1610,7 +1607,7 @@ static long long exact_batch_blocks(int cap) {
 // Builds the host image of the table part of a batch workspace.  Returns the bytes
 // of workspace the batch needs (0 on a batch-level argument error).
 static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const voxtet_opts &o, char *ws_dev,
-                                std::vector<char> *image, int *host_status, int *cull_kind = nullptr) {
+                                std::vector<char> *image, int *host_status) {
   const BatchLayout L = batch_layout(cap);
   size_t need = L.o_slices;
   std::vector<int> ok(n);
@@ -1697,15 +1694,7 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
   vbase[n] = vsum;
   zbase[n] = zsum;
   bbase[n] = bsum;
-  if (cull_kind) {  // which tile paths the jobs with tets need
-    int with = 0, without = 0;
-    for (int j = 0; j < n; ++j) {
-      if (!ok[j] || jobs[j].n_tets == 0) continue;
-      if (tab[j].p.cull) ++with;
-      else ++without;
-    }
-    *cull_kind = with && without ? kCullPerJob : (with ? kCullAll : kCullNone);
-  }
+
   bh->n_jobs = n;
   bh->total_tiles = tsum;
   bh->total_verts = vsum;
@@ -1715,17 +1704,14 @@ static size_t build_batch_image(const voxtet_job *jobs, int n, int cap, const vo
 
 typedef void (*BatchVoxKernel)(BatchHeader *, const JobDesc *, const unsigned long long *);
 
-static BatchVoxKernel batch_vox_kernel(bool strict, int cull) {
-  if (strict)
-    return cull == kCullNone ? k_voxelize_batched<true, kCullNone>
-                             : (cull == kCullAll ? k_voxelize_batched<true, kCullAll> : k_voxelize_batched<true, kCullPerJob>);
-  return cull == kCullNone ? k_voxelize_batched<false, kCullNone>
-                           : (cull == kCullAll ? k_voxelize_batched<false, kCullAll> : k_voxelize_batched<false, kCullPerJob>);
+static BatchVoxKernel batch_vox_kernel(bool strict, bool cull) {
+  if (strict) return cull ? k_voxelize_batched<true, true> : k_voxelize_batched<true, false>;
+  return cull ? k_voxelize_batched<false, true> : k_voxelize_batched<false, false>;
 }
 
-// Enqueues the batch kernels on `stream` (the table must already be uploaded); `cull` is the
-// batch's BatchCull kind (build_batch_image).
-static int launch_batch(char *ws, int cap, int strict, int cull, cudaStream_t stream) {
+// Enqueues the batch kernels on `stream` (the table must already be uploaded); `cull`: the
+// batch's jobs skip rows outside each slice's cross-section (opts->row_cull != 2).
+static int launch_batch(char *ws, int cap, int strict, bool cull, cudaStream_t stream) {
   DeviceInfo *dev = nullptr;
   if (device_info(dev) != cudaSuccess) return VOXTET_ERR_CUDA;
   const BatchLayout L = batch_layout(cap);
@@ -1774,7 +1760,7 @@ struct voxtet_plan {
   char *pinned = nullptr;  // host image of the table part, uploaded by the graph
   size_t image_bytes = 0;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t exec[3] = {nullptr, nullptr, nullptr};  // one graph per BatchCull kind, captured on first use
+  cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
   bool in_flight = false;
   int n_jobs = 0;
@@ -1802,14 +1788,12 @@ int voxelize_tets_batched(const voxtet_job *jobs, int32_t n_jobs, void *d_ws, si
   const int cap = n_jobs > 0 ? n_jobs : 1;
   std::vector<int> hs((size_t)cap, VOXTET_OK);
   std::vector<char> image;
-  int cull = kCullPerJob;
-  const size_t need =
-      build_batch_image(jobs, n_jobs, cap, o, reinterpret_cast<char *>(d_ws), &image, hs.data(), &cull);
+  const size_t need = build_batch_image(jobs, n_jobs, cap, o, reinterpret_cast<char *>(d_ws), &image, hs.data());
   if (need > ws_bytes) return VOXTET_ERR_WORKSPACE;
   cudaStream_t stream = reinterpret_cast<cudaStream_t>(stream_);
   if (cudaMemcpyAsync(d_ws, image.data(), image.size(), cudaMemcpyHostToDevice, stream) != cudaSuccess)
     return VOXTET_ERR_CUDA;
-  st = launch_batch(reinterpret_cast<char *>(d_ws), cap, o.mode == 1, cull, stream);
+  st = launch_batch(reinterpret_cast<char *>(d_ws), cap, o.mode == 1, o.row_cull != 2, stream);
   if (st != VOXTET_OK) return st;
   if (o.sync) {
     st = read_job_status(reinterpret_cast<char *>(d_ws), cap, n_jobs, hs.data(), stream);
@@ -1853,17 +1837,16 @@ int voxtet_plan_run(voxtet_plan *p, const voxtet_job *jobs, int32_t n_jobs, void
   p->in_flight = false;
   p->host_status.assign((size_t)(n_jobs > 0 ? n_jobs : 1), VOXTET_OK);
   std::vector<char> image;
-  int cull = kCullPerJob;
-  const size_t need = build_batch_image(jobs, n_jobs, p->cap, p->opts, p->ws, &image, p->host_status.data(), &cull);
+  const size_t need = build_batch_image(jobs, n_jobs, p->cap, p->opts, p->ws, &image, p->host_status.data());
   if (need > p->ws_bytes) return VOXTET_ERR_NOMEM;
   std::memcpy(p->pinned, image.data(), p->image_bytes);
-  cudaGraphExec_t &exec = p->exec[cull];
-  if (!exec) {  // capture the upload and the kernels once per kind; later runs replay them
+  cudaGraphExec_t &exec = p->exec;
+  if (!exec) {  // capture the upload and the kernels once; later runs replay them
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return VOXTET_ERR_CUDA;
     cudaMemcpyAsync(p->ws, p->pinned, p->image_bytes, cudaMemcpyHostToDevice, p->cap_stream);
     const unsigned long long before = g_launches.load();
-    const int st = launch_batch(p->ws, p->cap, p->opts.mode == 1, cull, p->cap_stream);
+    const int st = launch_batch(p->ws, p->cap, p->opts.mode == 1, p->opts.row_cull != 2, p->cap_stream);
     g_launches.store(before);  // captured, not launched
     if (cudaStreamEndCapture(p->cap_stream, &g) != cudaSuccess || st != VOXTET_OK) {
       if (g) cudaGraphDestroy(g);
@@ -1908,8 +1891,7 @@ int voxtet_plan_query(voxtet_plan *p) {
 void voxtet_plan_destroy(voxtet_plan *p) {
   if (!p) return;
   if (p->in_flight && p->done) cudaEventSynchronize(p->done);
-  for (cudaGraphExec_t &e : p->exec)
-    if (e) cudaGraphExecDestroy(e);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
   if (p->done) cudaEventDestroy(p->done);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->pinned) cudaFreeHost(p->pinned);

@@ -68,10 +68,6 @@ class Arena:
         return self.buf[off:off + n].view(dtype=__import__("torch").int32).view(res, res, w)
 
 
-CULL_MIN_RES = 1  # grid side from which a job skips rows outside each z-slice's cross-section (the
-                  # library's automatic choice: every grid)
-
-
 def grid_bytes(res: int) -> int:
     return res * res * ((res + 31) // 32) * 4
 
@@ -214,27 +210,17 @@ class Server:
             for si, sl in enumerate(self.slots):
                 if sl.busy or not admitted:
                     continue
-                # a batch of one culling kind (grids from CULL_MIN_RES per side skip rows outside
-                # each cross-section, smaller ones do not): such a batch runs the kernel with only
-                # that tile path compiled in; requests of the other kind keep their queue order
-                # (with the automatic choice every request is of one kind)
                 specs, group, used = [], [], self.table_bytes
-                kind = admitted[0].res >= CULL_MIN_RES
-                rest = deque()
                 while admitted and len(group) < self.max_jobs:
-                    tk = admitted.popleft()
-                    if (tk.res >= CULL_MIN_RES) != kind:
-                        rest.append(tk)
-                        continue
+                    tk = admitted[0]
                     need = self._slice_bytes(tk.mesh_id, tk.res)
                     if group and used + need > sl.ws_bytes:
-                        admitted.appendleft(tk)
                         break
+                    admitted.popleft()
                     used += need
                     group.append(tk)
                     specs.append(vb.JobSpec(self.meshes[tk.mesh_id], tk.res, self.arena.view_grid(tk.grid_off, tk.res),
                                             span_rows=self.span_rows_by_res.get(tk.res, 0)))
-                admitted.extendleft(reversed(rest))
                 st = sl.plan.run(specs, stream=sl.stream)
                 if st != vt.OK:
                     raise vt.VoxtetError(st, "a single request does not fit a slot's workspace")

@@ -79,28 +79,33 @@ def test_plan_replays_with_different_batches(env, workload, mode):
         plan.close()
 
 
-def test_plan_batches_of_each_culling_kind(env, workload):
-    """A batch whose jobs all skip rows outside the cross-sections (grids from 256 per side),
-    one whose jobs never do, and a mix: each kind runs its own compiled tile path and the plan
-    keeps a graph per kind; every grid equals the job's single call, in any order of runs."""
+@pytest.mark.parametrize("row_cull", [1, 2])
+def test_batches_with_culling_on_and_off(env, workload, row_cull):
+    """A batch's jobs share one culling choice, and each choice runs a kernel with only its tile
+    path compiled in: with rows outside the cross-sections skipped (1) and visited (2), every
+    grid of a plan (replayed with another batch in between) and of a one-off batched call
+    equals the job's single call with the same choice."""
     vt, batch = env
-    small = [j for j in workload if j.res < 256][:10]
-    large = [j for j in workload if j.res >= 256][:4]
-    assert small and large
-    kinds = [_specs(batch, vt, small), _specs(batch, vt, large), _specs(batch, vt, small[:5] + large[:2])]
-    need = max(batch.batch_workspace_size(s, 16) for s in kinds)
-    plan = batch.Plan(need, 16)
+    jobs_a, jobs_b = workload[:12], workload[12:30]
+    kinds = [_specs(batch, vt, jobs_a), _specs(batch, vt, jobs_b)]
+    need = max(batch.batch_workspace_size(s, 32) for s in kinds)
+    plan = batch.Plan(need, 32, row_cull=row_cull)
     try:
-        for specs in (kinds[0], kinds[1], kinds[2], kinds[0], kinds[2]):
+        for specs in (kinds[0], kinds[1], kinds[0]):
             for sp in specs:
                 sp.out.fill_(-1)
             assert plan.run(specs) == vt.OK
             assert plan.wait() == [vt.OK] * len(specs)
             for sp in specs:
-                ref = vt.voxelize(sp.mesh.verts, sp.mesh.tets, sp.origin, sp.voxel_size, sp.res)
+                ref = vt.voxelize(sp.mesh.verts, sp.mesh.tets, sp.origin, sp.voxel_size, sp.res, row_cull=row_cull)
                 assert bool((sp.out == ref).all()), sp.res
     finally:
         plan.close()
+    specs = _specs(batch, vt, jobs_b, fill=-1)
+    assert batch.voxelize_batched(specs, row_cull=row_cull) == [vt.OK] * len(specs)
+    for sp in specs:
+        ref = vt.voxelize(sp.mesh.verts, sp.mesh.tets, sp.origin, sp.voxel_size, sp.res, row_cull=row_cull)
+        assert bool((sp.out == ref).all()), sp.res
 
 
 def test_plan_reports_workspace_overflow(env, workload):
